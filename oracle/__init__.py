@@ -1,0 +1,222 @@
+"""CPU oracle for the exact GF(p) dot product and its derived products.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by the smoke check and by
+the CPU-baseline leg of the benchmark, never by the library.  It shares no code
+with the CUDA path; the C source is ``gfp_oracle.c`` in this directory (per
+term Zpz arithmetic, Section 2.1 of the paper), compiled with the host C
+compiler by :func:`build` into ``oracle/_build/liboracle.so``.
+
+All entry points take numpy uint32 arrays of canonical residues (< p).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gfp_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+
+_lib = None
+_lock = threading.Lock()
+
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C compiler (plain -O2, no -march)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or \
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"],
+                       check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_dot.restype = ctypes.c_uint32
+            lib.oracle_dot.argtypes = [ctypes.c_uint32, ctypes.c_uint64, _u32p, _u32p]
+            lib.oracle_dot_batch.restype = None
+            lib.oracle_dot_batch.argtypes = [ctypes.c_uint64, _u32p, _u64p, _u64p, _u32p, _u32p,
+                                             _u32p]
+            lib.oracle_matvec_rows.restype = None
+            lib.oracle_matvec_rows.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                               ctypes.c_uint64, _u32p, ctypes.c_uint64, _u32p,
+                                               _u32p]
+            lib.oracle_block_rows.restype = None
+            lib.oracle_block_rows.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                              ctypes.c_uint64, ctypes.c_uint64, _u32p,
+                                              ctypes.c_uint64, _u32p, ctypes.c_uint64, _u32p,
+                                              ctypes.c_uint64]
+            lib.oracle_csr_rows.restype = None
+            lib.oracle_csr_rows.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                            ctypes.c_uint64, _u32p, _u32p, _u32p, _u32p,
+                                            ctypes.c_uint64, _u32p, ctypes.c_uint64]
+            lib.oracle_paper_block_dot.restype = ctypes.c_uint64
+            lib.oracle_paper_block_dot.argtypes = [ctypes.c_uint32, ctypes.c_uint64, _u32p, _u32p,
+                                                   ctypes.c_uint64, ctypes.c_int]
+            lib.oracle_paper_overflow_dot.restype = ctypes.c_uint32
+            lib.oracle_paper_overflow_dot.argtypes = [ctypes.c_uint32, ctypes.c_uint64, _u32p,
+                                                      _u32p]
+            lib.oracle_paper_fp_reduce.restype = ctypes.c_double
+            lib.oracle_paper_fp_reduce.argtypes = [ctypes.c_double, ctypes.c_double]
+            lib.oracle_paper_fp_dot.restype = ctypes.c_uint32
+            lib.oracle_paper_fp_dot.argtypes = [ctypes.c_uint32, ctypes.c_uint64, _u32p, _u32p,
+                                                ctypes.c_uint64]
+            _lib = lib
+    return _lib
+
+
+def _p32(a: np.ndarray):
+    assert a.dtype == np.uint32 and a.flags.c_contiguous
+    return a.ctypes.data_as(_u32p)
+
+
+def _p64(a: np.ndarray):
+    assert a.dtype == np.uint64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_u64p)
+
+
+def _threads(n: int | None) -> int:
+    return n or max(1, len(os.sched_getaffinity(0)))
+
+
+def dot(p: int, x: np.ndarray, y: np.ndarray) -> int:
+    """(sum x_i*y_i) mod p, term by term."""
+    x = np.ascontiguousarray(x, dtype=np.uint32)
+    y = np.ascontiguousarray(y, dtype=np.uint32)
+    assert x.shape == y.shape
+    return int(_load().oracle_dot(p, x.shape[0], _p32(x), _p32(y)))
+
+
+def dot_batch(ps, lens, offs, x: np.ndarray, y: np.ndarray, threads: int | None = None):
+    """Residues of packed pairs (pair j at offs[j], length lens[j], prime ps[j])."""
+    lib = _load()
+    ps = np.ascontiguousarray(ps, dtype=np.uint32)
+    lens = np.ascontiguousarray(lens, dtype=np.uint64)
+    offs = np.ascontiguousarray(offs, dtype=np.uint64)
+    x = np.ascontiguousarray(x, dtype=np.uint32)
+    y = np.ascontiguousarray(y, dtype=np.uint32)
+    count = ps.shape[0]
+    out = np.zeros(count, dtype=np.uint32)
+    nth = _threads(threads)
+    # split pairs into nth contiguous groups of similar total length
+    bounds = np.searchsorted(np.cumsum(lens.astype(np.float64)),
+                             np.linspace(0, float(lens.sum()), nth + 1)[1:-1])
+    edges = [0] + [int(b) for b in bounds] + [count]
+
+    def run(g):
+        a, b = edges[g], edges[g + 1]
+        if b > a:
+            lib.oracle_dot_batch(b - a, _p32(ps[a:b]), _p64(lens[a:b]), _p64(offs[a:b]),
+                                 _p32(x), _p32(y), _p32(out[a:b]))
+    with ThreadPoolExecutor(nth) as ex:
+        list(ex.map(run, range(len(edges) - 1)))
+    return out
+
+
+def _row_split(rows: int, nth: int):
+    step = max(1, -(-rows // nth))
+    return [(r, min(rows, r + step)) for r in range(0, rows, step)]
+
+
+def matvec(p: int, A: np.ndarray, x: np.ndarray, rows: range | None = None,
+           threads: int | None = None) -> np.ndarray:
+    """y = A x mod p for a row-major uint32 matrix (all rows, or ``rows``)."""
+    lib = _load()
+    A = np.ascontiguousarray(A, dtype=np.uint32)
+    x = np.ascontiguousarray(x, dtype=np.uint32)
+    m, k = A.shape
+    assert x.shape == (k,)
+    y = np.zeros(m, dtype=np.uint32)
+    r0, r1 = (0, m) if rows is None else (rows.start, rows.stop)
+
+    def run(rr):
+        lib.oracle_matvec_rows(p, rr[0], rr[1], k, _p32(A), k, _p32(x), _p32(y))
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(run, [(r0 + a, r0 + b) for a, b in _row_split(r1 - r0, _threads(threads))]))
+    return y
+
+
+def block(p: int, A: np.ndarray, B: np.ndarray, threads: int | None = None) -> np.ndarray:
+    """C = A B mod p, A m x k and B k x nb row-major uint32."""
+    lib = _load()
+    A = np.ascontiguousarray(A, dtype=np.uint32)
+    B = np.ascontiguousarray(B, dtype=np.uint32)
+    m, k = A.shape
+    k2, nb = B.shape
+    assert k == k2
+    C = np.zeros((m, nb), dtype=np.uint32)
+
+    def run(rr):
+        lib.oracle_block_rows(p, rr[0], rr[1], k, nb, _p32(A), k, _p32(B), nb, _p32(C), nb)
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(run, _row_split(m, _threads(threads))))
+    return C
+
+
+def block_rows(p: int, A: np.ndarray, B: np.ndarray, rows) -> np.ndarray:
+    """Selected rows of A B mod p (rows: iterable of row indices)."""
+    rows = np.asarray(list(rows), dtype=np.int64)
+    return block(p, np.ascontiguousarray(A[rows]), B, threads=1)
+
+
+def csr(p: int, row_ptr, col, val, B: np.ndarray, threads: int | None = None) -> np.ndarray:
+    """C = A B mod p for a CSR matrix A (row_ptr, col, val) and dense B."""
+    lib = _load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.uint32)
+    col = np.ascontiguousarray(col, dtype=np.uint32)
+    val = np.ascontiguousarray(val, dtype=np.uint32)
+    B = np.ascontiguousarray(B, dtype=np.uint32)
+    m = row_ptr.shape[0] - 1
+    nb = B.shape[1]
+    C = np.zeros((m, nb), dtype=np.uint32)
+    if col.shape[0] == 0:
+        col = np.zeros(1, np.uint32)
+        val = np.zeros(1, np.uint32)
+
+    def run(rr):
+        lib.oracle_csr_rows(p, rr[0], rr[1], nb, _p32(row_ptr), _p32(col), _p32(val), _p32(B),
+                            nb, _p32(C), nb)
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(run, _row_split(m, _threads(threads))))
+    return C
+
+
+# ---- the paper's variants, restated (Sections 2.3, 3.1-3.3) ----
+
+def paper_block_dot(p: int, x, y, K: int, acc_bits: int = 64):
+    x = np.ascontiguousarray(x, dtype=np.uint32)
+    y = np.ascontiguousarray(y, dtype=np.uint32)
+    r = int(_load().oracle_paper_block_dot(p, x.shape[0], _p32(x), _p32(y), K, acc_bits))
+    return None if r == (1 << 64) - 1 else r
+
+
+def paper_overflow_dot(p: int, x, y) -> int:
+    x = np.ascontiguousarray(x, dtype=np.uint32)
+    y = np.ascontiguousarray(y, dtype=np.uint32)
+    return int(_load().oracle_paper_overflow_dot(p, x.shape[0], _p32(x), _p32(y)))
+
+
+def paper_fp_reduce(T: float, P: float) -> float:
+    return float(_load().oracle_paper_fp_reduce(T, P))
+
+
+def paper_fp_dot(p: int, x, y, K: int):
+    x = np.ascontiguousarray(x, dtype=np.uint32)
+    y = np.ascontiguousarray(y, dtype=np.uint32)
+    r = int(_load().oracle_paper_fp_dot(p, x.shape[0], _p32(x), _p32(y), K))
+    return None if r == 0xFFFFFFFF else r
