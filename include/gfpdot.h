@@ -1,0 +1,243 @@
+/*
+ * libgfpdot — exact dot products over word-size prime fields GF(p) on GB300.
+ *
+ * The method is J.-G. Dumas, "Efficient dot product over word-size finite
+ * fields": residues are multiplied and accumulated unreduced and reduced
+ * modulo p only when the accumulator could overflow (delayed division,
+ * Section 3.1, Eq. (1); blocked form, Section 3.2; division on demand by
+ * overflow detection, Section 3.3; hybrid, Section 3.4, Eq. (2)), with one
+ * final reduction into [0, p).  Every call returns the exact residue: the
+ * result of each entry point is bit-identical to the plain definition
+ * (sum x_i*y_i) mod p, whatever representation computes it.
+ *
+ * Conventions (all entry points)
+ *  - Residues are uint32_t and must be canonical (0 <= v < p).  Non-canonical
+ *    inputs are outside the contract; with validation enabled
+ *    (gfp_set_validate or GFP_VALIDATE=1) the operand-checking entry points
+ *    detect them on the device and return GFP_ERR_RANGE (this adds a device
+ *    synchronisation, so it is not usable under stream capture).
+ *  - The modulus p satisfies 2 <= p <= 2^32-1.  Primality is not required by
+ *    the arithmetic (results are residues modulo p), but the method is stated
+ *    for prime fields and the tests use primes.
+ *  - Pointer arguments named "device" are CUDA device pointers (4-byte
+ *    aligned; 16-byte alignment enables the 128-bit load path, other
+ *    alignments fall back to 32-bit loads inside the same kernel).  Pointers
+ *    named "host" are host memory.  The caller owns every operand and output
+ *    buffer; they must stay alive until the work queued on `stream` completes.
+ *    The library owns only the context/plan/server objects it creates and
+ *    never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Compute entry points only enqueue work: they return before the
+ *    result is ready unless documented otherwise.
+ *  - Errors: argument checks happen before any launch and return a negative
+ *    status with nothing enqueued.  Launch failures return GFP_ERR_CUDA.
+ *    Asynchronous device errors surface on a later call that synchronises.
+ *    No exception crosses this interface and nothing aborts the process.
+ */
+#ifndef GFPDOT_H
+#define GFPDOT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GFP_API __attribute__((visibility("default")))
+#else
+#define GFP_API
+#endif
+
+typedef enum gfp_status {
+    GFP_OK = 0,
+    GFP_PENDING = 1,             /* service: job not finished yet */
+    GFP_ERR_INVALID = -1,        /* NULL pointer, p < 2, bad dimensions or strides */
+    GFP_ERR_RANGE = -2,          /* an input residue >= p (validation enabled) */
+    GFP_ERR_UNSUPPORTED = -3,    /* requested representation not eligible for p */
+    GFP_ERR_NOMEM = -4,          /* device or host allocation failed */
+    GFP_ERR_CUDA = -5,           /* a CUDA runtime call or launch failed */
+    GFP_ERR_AGAIN = -6,          /* service queue full */
+    GFP_ERR_TIMEOUT = -7,        /* a bounded wait ran out */
+    GFP_ERR_UNKNOWN_TICKET = -8, /* service: no such ticket */
+    GFP_ERR_CANCELLED = -9       /* service: job cancelled or server shut down */
+} gfp_status;
+
+/* Accumulation representation of the dot-product kernels. */
+typedef enum gfp_repr {
+    GFP_REPR_AUTO = 0,      /* per-(p, n) choice from the tuned plan or the default rules */
+    GFP_REPR_PERTERM = 1,   /* classical Zpz: one remainder per term (Section 2.1); baseline */
+    GFP_REPR_U64_BLOCK = 2, /* 64-bit accumulator reduced every k terms (Sections 3.1-3.2,
+                               k from Eq. (2) with the residue carried between blocks) */
+    GFP_REPR_U64_CARRY = 3, /* division on demand (Section 3.3): 64-bit sum that may wrap, a
+                               32-bit wrap count, and one correction by 2^64 mod p at the end */
+    GFP_REPR_FP64 = 4,      /* 53-bit exact double accumulator reduced every k terms with the
+                               floating-point reduction of Section 2.3 (p <= 94906266 only) */
+    GFP_REPR_COUNT_ = 5
+} gfp_repr;
+
+typedef struct gfp_ctx gfp_ctx;
+
+/* Per-modulus constants (Section 3, host side). */
+typedef struct gfp_params {
+    uint32_t p;
+    uint32_t corr;        /* CORR = 2^64 mod p (Section 3.3 with m = 64) */
+    uint64_t k_u64;       /* Eq. (2), m = 64: largest k with k(p-1)^2 + (p-1) < 2^64 */
+    uint64_t k_fp64;      /* Eq. (2), m = 53: largest k with k(p-1)^2 + (p-1) < 2^53; 0 if none */
+    uint64_t barrett_mu;  /* floor(2^64 / p), Barrett's reduction constant */
+    double   inv_p;       /* 1/p rounded to double (Section 2.3) */
+    int      fp64_ok;     /* 1 when k_fp64 >= 1 */
+} gfp_params;
+
+/* ---- status and parameters (host only; usable without a GPU) ---- */
+
+/* Static string naming a status code. */
+GFP_API const char *gfp_status_string(int status);
+
+/* Largest number of products lambda that an acc_bits-wide unsigned
+ * accumulator can absorb before a reduction is required (Section 3.1,
+ * Eq. (1): lambda (p-1)^2 < 2^m; with carried != 0, Section 3.4, Eq. (2) in its
+ * tight form lambda (p-1)^2 + (p-1) < 2^m, for a block that starts from a
+ * residue already reduced below p).  acc_bits in [1, 64].  Returns 0 when no
+ * product fits, or for invalid arguments (p < 2, acc_bits out of range). */
+GFP_API uint64_t gfp_delay_bound(uint32_t p, int acc_bits, int carried);
+
+/* Fill *out with the constants above.  GFP_ERR_INVALID if p < 2 or out NULL. */
+GFP_API gfp_status gfp_get_params(uint32_t p, gfp_params *out);
+
+/* Host evaluation of the library's reductions (the same inline code the
+ * kernels use), for testing: x mod p by Barrett's method, and the
+ * floating-point reduction of Section 2.3 of an integral 0 <= T <= 2^53. */
+GFP_API uint32_t gfp_reduce_u64(uint64_t x, uint32_t p);
+GFP_API double   gfp_reduce_f64(double T, uint32_t p);
+
+/* Representation that GFP_REPR_AUTO resolves to for (p, n) in `ctx`
+ * (ctx may be NULL for the built-in rules). */
+GFP_API gfp_repr gfp_choose_repr(const gfp_ctx *ctx, uint32_t p, uint64_t n);
+
+/* ---- context ---- */
+
+/* Create a context bound to CUDA device `device`; allocates its workspace
+ * (a few MB).  *out receives the handle.  GFP_ERR_CUDA if the device is
+ * unavailable.  Reads GFP_PLAN_FILE (tuned plan), GFP_FORCE_REPR (0..4) and
+ * GFP_VALIDATE (0/1) from the environment. */
+GFP_API gfp_status gfp_context_create(int device, gfp_ctx **out);
+/* Synchronise the context's work, free its workspace and the handle. */
+GFP_API gfp_status gfp_context_destroy(gfp_ctx *ctx);
+/* Force a representation for later calls (GFP_REPR_AUTO restores the
+ * automatic choice).  Calls whose p is not eligible then fail with
+ * GFP_ERR_UNSUPPORTED. */
+GFP_API gfp_status gfp_set_repr(gfp_ctx *ctx, gfp_repr repr);
+/* Enable (1) or disable (0) device-side input validation. */
+GFP_API gfp_status gfp_set_validate(gfp_ctx *ctx, int on);
+/* Number of kernels this context has launched so far (diagnostics). */
+GFP_API uint64_t gfp_launch_count(const gfp_ctx *ctx);
+
+/* ---- dot products ---- */
+
+/* out[0] = (sum_{i<n} x[i]*y[i]) mod p.
+ *   x, y: device, n residues each.  out: device, one uint32_t.
+ * n == 0 writes 0.  One kernel launch; uses one slot of the context's scratch
+ * ring (calls in flight at the same time on different streams take different
+ * slots; more than 1024 such calls in flight at once would share a slot). */
+GFP_API gfp_status gfp_dot(gfp_ctx *ctx, uint32_t p, uint64_t n, const uint32_t *x,
+                           const uint32_t *y, uint32_t *out, void *stream);
+
+/* One pair of a batch: x, y device pointers of n residues modulo p. */
+typedef struct gfp_dot_desc {
+    uint32_t p;
+    uint32_t repr;          /* gfp_repr for this pair; GFP_REPR_AUTO for the context's choice */
+    uint64_t n;
+    const uint32_t *x;
+    const uint32_t *y;
+} gfp_dot_desc;
+
+/* out[j] = dot of pair d[j] modulo d[j].p for 0 <= j < count, in ONE
+ * persistent kernel launch over a work list of (pair, chunk) units of uneven
+ * lengths and mixed moduli.  d: host array.  out: device, count uint32_t.
+ * Builds the work list on the host and uploads it into the context's
+ * workspace (pageable copy: not usable under stream capture; use a plan).
+ * Calls sharing one context must not overlap on different streams. */
+GFP_API gfp_status gfp_dot_batched(gfp_ctx *ctx, const gfp_dot_desc *d, uint64_t count,
+                                   uint32_t *out, void *stream);
+
+/* Reusable batch plan: the work list and its scratch live on the device, so
+ * gfp_batch_plan_exec is a single kernel launch, capture-safe, with no host
+ * work.  The descriptors (pointers, lengths, moduli) are fixed at creation;
+ * the operand contents may change between executions.  One plan must not be
+ * executed concurrently on two streams (its scratch counters are shared). */
+typedef struct gfp_batch_plan gfp_batch_plan;
+GFP_API gfp_status gfp_batch_plan_create(gfp_ctx *ctx, const gfp_dot_desc *d, uint64_t count,
+                                         gfp_batch_plan **out);
+GFP_API gfp_status gfp_batch_plan_exec(gfp_batch_plan *plan, uint32_t *out, void *stream);
+/* Units in the plan's work list and algorithmic operand bytes per execution. */
+GFP_API gfp_status gfp_batch_plan_info(const gfp_batch_plan *plan, uint64_t *units,
+                                       uint64_t *bytes);
+GFP_API gfp_status gfp_batch_plan_destroy(gfp_batch_plan *plan);
+
+/* Batched dot products from HOST buffers (end-to-end form): pair j is
+ * x_host[off[j] .. off[j]+n[j]) and y_host[...] modulo p[j]; all arrays are
+ * host memory (pinned memory gives full copy bandwidth).  The call copies
+ * the `total` elements of x_host and y_host to the device, runs the batched
+ * kernel, copies the count residues back into out_host and synchronises
+ * `stream` before returning.  off[j] must be a multiple of 4 and
+ * off[j] + n[j] <= total.  Device staging is held by the context and grown on
+ * demand. */
+GFP_API gfp_status gfp_dot_batched_host(gfp_ctx *ctx, uint64_t count, const uint32_t *p,
+                                        const uint64_t *n, const uint64_t *off,
+                                        const uint32_t *x_host, const uint32_t *y_host,
+                                        uint64_t total, uint32_t *out_host, void *stream);
+
+/* ---- matrix-vector (the iterative use named in Section 1) ---- */
+
+/* y[i] = (sum_j A[i*lda + j] * x[j]) mod p for 0 <= i < rows.
+ *   A: device, row-major, lda >= cols.  x: device, cols.  y: device, rows.
+ * y must not overlap A or x.  One kernel launch. */
+GFP_API gfp_status gfp_matvec(gfp_ctx *ctx, uint32_t p, uint64_t rows, uint64_t cols,
+                              const uint32_t *A, uint64_t lda, const uint32_t *x, uint32_t *y,
+                              void *stream);
+
+/* Wiedemann-style iteration x_{t+1} = A x_t for t = 0 .. iters-1 with a square
+ * n x n matrix, all launches captured once in a CUDA graph (cached in the
+ * context per argument set) and replayed with one graph launch.
+ *   x0: device, n.  Y: device, iters*n; row t receives x_{t+1}. */
+GFP_API gfp_status gfp_matvec_iterate(gfp_ctx *ctx, uint32_t p, uint64_t n, const uint32_t *A,
+                                      uint64_t lda, const uint32_t *x0, uint32_t *Y,
+                                      uint32_t iters, void *stream);
+
+/* ---- install-time tuning (automated empirical optimisation, Section 4) ---- */
+
+/* Time every eligible representation (U64_BLOCK, U64_CARRY, FP64) and
+ * work-unit length (16Ki, 64Ki, 256Ki elements) for each prime of
+ * primes[0..nprimes) (NULL: 32749, 65521, 67108859, 2^31-1, 2^32-5) and
+ * each length 2^lg, lg = lg_lo, lg_lo+2, ..., <= lg_hi (lg_hi <= 26), on
+ * batches of resident synthetic vectors (512 MiB of operands), and record the
+ * fastest choice per (p, floor(log2 n)) in the context's plan; GFP_REPR_AUTO
+ * calls consult it (nearest length bucket of the same p).  Writes the plan to
+ * plan_path when it is not NULL.  Synchronous; allocates while it runs. */
+GFP_API gfp_status gfp_tune(gfp_ctx *ctx, const uint32_t *primes, uint32_t nprimes,
+                            uint32_t lg_lo, uint32_t lg_hi, const char *plan_path);
+/* Replace the context's plan by the one in `path` / write it to `path`
+ * (format: {"version": 1, "entries": [{"p":P, "lg_n":L, "repr":R, "chunk":C}, ...]}).
+ * GFP_ERR_INVALID if the file cannot be read or parsed (plan unchanged). */
+GFP_API gfp_status gfp_plan_load(gfp_ctx *ctx, const char *path);
+GFP_API gfp_status gfp_plan_save(const gfp_ctx *ctx, const char *path);
+/* Number of (p, length bucket) entries in the context's plan. */
+GFP_API uint64_t gfp_plan_size(const gfp_ctx *ctx);
+
+/* ---- synthetic inputs (device generator) ---- */
+
+/* out[i] = word(seed, stream_id, offset + i) mod p for 0 <= i < n, where
+ * word is the counter-based SplitMix64 sequence
+ *   key = mix64(seed + G*(stream_id+1)),  word(i) = mix64(key + G*(i+1)),
+ *   G = 0x9E3779B97F4A7C15  (arithmetic modulo 2^64).
+ * Input synthesis only (the benchmark and service generate operands with
+ * it); it is not part of the dot-product method. */
+GFP_API gfp_status gfp_fill_uniform(uint32_t p, uint64_t seed, uint64_t stream_id,
+                                    uint64_t offset, uint64_t n, uint32_t *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFPDOT_H */

@@ -1,0 +1,126 @@
+// Internal declarations shared by the translation units of libgfpdot.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "gfp_arith.cuh"
+#include "../../include/gfpdot.h"
+
+namespace gfp {
+
+// One pair of a batch as the persistent kernel sees it (64 bytes).
+struct DevPair {
+    const uint32_t *x;
+    const uint32_t *y;
+    uint64_t n;
+    uint64_t k;        // reduction interval for the chosen representation
+    Mod m;             // 32 bytes
+};
+static_assert(sizeof(Mod) == 32, "Mod layout");
+
+// Representation and unit count are kept beside the pair (read once per unit).
+struct DevPairAux {
+    uint32_t repr;
+    uint32_t units;
+};
+
+// One work unit: elements [begin, end) of pair `pair`.
+struct DevUnit {
+    uint64_t begin;
+    uint64_t end;
+    uint32_t pair;
+    uint32_t pad;
+};
+
+Mod make_mod(uint32_t p);
+uint64_t delay_bound(uint32_t p, int acc_bits, int carried);
+uint64_t k_for(Repr r, uint32_t p);
+bool repr_eligible(Repr r, uint32_t p);
+
+// Launch configuration constants of the dot kernels.
+constexpr int DOT_THREADS = 256;
+constexpr int MV_THREADS = 1024;
+
+// Device scratch of one batched execution.
+struct BatchScratch {
+    unsigned long long *slots = nullptr;  // per pair: sum of unit residues
+    uint32_t *tickets = nullptr;          // per pair: finished units
+    uint32_t *ctr = nullptr;              // [0] next unit, [1] finished CTAs
+};
+
+// Kernel launchers (gfp_dot.cu, gfp_matvec.cu).
+cudaError_t launch_dot_single(Repr r, const Mod &m, uint64_t k, uint64_t n, const uint32_t *x,
+                              const uint32_t *y, unsigned long long *slot, uint32_t *ticket,
+                              uint32_t *out, int grid, cudaStream_t s);
+int dot_single_grid(Repr r, uint64_t n, int sm_count);
+cudaError_t launch_dot_batched(const DevPair *pairs, const DevPairAux *aux, const DevUnit *units,
+                               uint32_t n_units, BatchScratch sc, uint32_t *out, int grid,
+                               cudaStream_t s);
+int dot_batched_grid(int sm_count);
+cudaError_t launch_fill_uniform(uint32_t p, uint64_t seed, uint64_t stream_id, uint64_t offset,
+                                uint64_t n, uint32_t *out, cudaStream_t s);
+cudaError_t launch_check_range(const uint32_t *v, uint64_t n, uint32_t p, uint32_t *flag,
+                               cudaStream_t s);
+cudaError_t launch_matvec(Repr r, const Mod &m, uint64_t k, uint64_t rows, uint64_t cols,
+                          const uint32_t *A, uint64_t lda, const uint32_t *x, uint32_t *y,
+                          int sm_count, cudaStream_t s);
+
+}  // namespace gfp
+
+// Tuned plan entry: representation and unit chunk per (p, length bucket).
+struct gfp_plan_entry {
+    uint32_t p;
+    uint32_t lg_n;      // bucket: floor(log2(n)), 0..63
+    uint32_t repr;
+    uint32_t chunk;     // work-unit length in elements for batched execution
+};
+
+struct gfp_ctx {
+    int device = 0;
+    int sm_count = 0;
+    gfp_repr forced = GFP_REPR_AUTO;
+    bool validate = false;
+    std::atomic<uint64_t> launches{0};
+    std::mutex mu;
+
+    // single-dot scratch ring
+    unsigned long long *ring_slots = nullptr;
+    uint32_t *ring_tickets = nullptr;
+    uint32_t ring_size = 1024;
+    std::atomic<uint32_t> ring_pos{0};
+
+    // validation flag (device) and pinned host mirror
+    uint32_t *d_flag = nullptr;
+
+    // one-shot batched workspace (grown on demand)
+    void *bw = nullptr;
+    size_t bw_bytes = 0;
+    size_t bw_slots_off = (size_t)-1;   // offset of the scratch region last cleared
+    // host-buffer staging for gfp_dot_batched_host
+    uint32_t *stage = nullptr;
+    size_t stage_elems = 0;
+    uint32_t *stage_out = nullptr;
+    size_t stage_out_elems = 0;
+
+    // tuned plan: (p, lg_n) -> entry
+    std::map<std::pair<uint32_t, uint32_t>, gfp_plan_entry> plan;
+    uint32_t default_chunk = 65536;
+
+    // cached matvec iteration graphs
+    struct GraphKey {
+        uint32_t p; uint64_t n; const uint32_t *A; uint64_t lda; const uint32_t *x0; uint32_t *Y;
+        uint32_t iters; int repr;
+        bool operator<(const GraphKey &o) const
+        {
+            return std::tie(p, n, A, lda, x0, Y, iters, repr) <
+                   std::tie(o.p, o.n, o.A, o.lda, o.x0, o.Y, o.iters, o.repr);
+        }
+    };
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+};

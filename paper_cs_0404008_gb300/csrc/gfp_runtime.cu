@@ -1,0 +1,668 @@
+// Host side of libgfpdot: per-modulus parameters (delay bounds of Eq. (1)
+// and Eq. (2), the overflow correction of Section 3.3, Barrett and
+// floating-point constants), the context and its scratch, representation
+// choice, batch work lists, and the C entry points of the dot-product and
+// matrix-vector paths.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "gfp_internal.h"
+
+namespace gfp {
+
+uint64_t delay_bound(uint32_t p, int acc_bits, int carried)
+{
+    if (p < 2 || acc_bits < 1 || acc_bits > 64) return 0;
+    typedef unsigned __int128 u128;
+    const u128 pm1 = (u128)(p - 1), sq = pm1 * pm1;
+    const u128 lim = ((u128)1 << acc_bits) - 1;   // the sum must stay <= 2^m - 1
+    const u128 extra = carried ? pm1 : 0;
+    if (lim < extra + sq) return 0;
+    const u128 k = (lim - extra) / sq;
+    return k > (u128)UINT64_MAX ? UINT64_MAX : (uint64_t)k;
+}
+
+Mod make_mod(uint32_t p)
+{
+    Mod m;
+    m.p = p;
+    m.corr = (uint32_t)((UINT64_MAX % p + 1) % p);
+    if ((p & (p - 1)) == 0) {   // power of two: floor(2^64/p) = 2^(64 - log2 p)
+        int lg = 0;
+        while ((1u << lg) != p) ++lg;
+        m.mu = 1ull << (64 - lg);
+    } else {
+        m.mu = UINT64_MAX / p;  // equals floor(2^64/p) when p does not divide 2^64
+    }
+    m.pd = (double)p;
+    m.invp = 1.0 / (double)p;
+    return m;
+}
+
+uint64_t k_for(Repr r, uint32_t p)
+{
+    switch (r) {
+    case U64_BLOCK: return delay_bound(p, 64, 1);
+    case FP64: return delay_bound(p, 53, 1);
+    default: return 0;
+    }
+}
+
+bool repr_eligible(Repr r, uint32_t p)
+{
+    if (p < 2) return false;
+    switch (r) {
+    case PERTERM:
+    case U64_CARRY: return true;
+    case U64_BLOCK: return delay_bound(p, 64, 1) >= 1;
+    case FP64: return delay_bound(p, 53, 1) >= 1;
+    default: return false;
+    }
+}
+
+}  // namespace gfp
+
+using namespace gfp;
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+
+#define GFP_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) return GFP_ERR_CUDA;          \
+    } while (0)
+
+static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static inline uint32_t lg2_floor(uint64_t n)
+{
+    uint32_t l = 0;
+    while (n >>= 1) ++l;
+    return l;
+}
+
+// Built-in rule: the blocked 64-bit form when its interval is so long that no
+// reduction happens inside a kernel, the wrap-counting form otherwise.
+static Repr default_repr(uint32_t p)
+{
+    return delay_bound(p, 64, 1) >= (1ull << 20) ? U64_BLOCK : U64_CARRY;
+}
+
+static const gfp_plan_entry *plan_lookup(const gfp_ctx *ctx, uint32_t p, uint64_t n)
+{
+    if (!ctx || ctx->plan.empty()) return nullptr;
+    auto it = ctx->plan.find({p, lg2_floor(n ? n : 1)});
+    if (it != ctx->plan.end()) return &it->second;
+    // nearest bucket of the same modulus
+    const gfp_plan_entry *best = nullptr;
+    uint32_t lg = lg2_floor(n ? n : 1), bd = 1000;
+    for (auto &kv : ctx->plan) {
+        if (kv.first.first != p) continue;
+        uint32_t d = kv.first.second > lg ? kv.first.second - lg : lg - kv.first.second;
+        if (d < bd) { bd = d; best = &kv.second; }
+    }
+    return best;
+}
+
+// Resolve the representation of one call; returns false if not eligible.
+static bool resolve_repr(const gfp_ctx *ctx, uint32_t requested, uint32_t p, uint64_t n, Repr *out)
+{
+    uint32_t r = requested;
+    if (r == GFP_REPR_AUTO && ctx) r = ctx->forced;
+    if (r == GFP_REPR_AUTO) {
+        const gfp_plan_entry *e = plan_lookup(ctx, p, n);
+        r = (e && repr_eligible((Repr)e->repr, p)) ? e->repr : default_repr(p);
+    }
+    if (r < GFP_REPR_PERTERM || r >= GFP_REPR_COUNT_) return false;
+    if (!repr_eligible((Repr)r, p)) return false;
+    *out = (Repr)r;
+    return true;
+}
+
+static uint32_t chunk_for(const gfp_ctx *ctx, uint32_t p, uint64_t n)
+{
+    const gfp_plan_entry *e = plan_lookup(ctx, p, n);
+    uint32_t c = (e && e->chunk) ? e->chunk : (ctx ? ctx->default_chunk : 65536u);
+    return std::max<uint32_t>(4096u, c & ~3u);
+}
+
+static gfp_status check_range(gfp_ctx *ctx, const uint32_t *v, uint64_t n, uint32_t p,
+                              cudaStream_t s)
+{
+    if (!ctx->validate || n == 0) return GFP_OK;
+    GFP_CUDA_TRY(cudaMemsetAsync(ctx->d_flag, 0, sizeof(uint32_t), s));
+    GFP_CUDA_TRY(launch_check_range(v, n, p, ctx->d_flag, s));
+    ctx->launches++;
+    uint32_t h = 0;
+    GFP_CUDA_TRY(cudaMemcpyAsync(&h, ctx->d_flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GFP_CUDA_TRY(cudaStreamSynchronize(s));
+    return h ? GFP_ERR_RANGE : GFP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batch work lists
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct HostBatch {
+    std::vector<DevPair> pairs;
+    std::vector<DevPairAux> aux;
+    std::vector<DevUnit> units;
+    uint64_t bytes = 0;
+};
+
+// Relative per-element cost used to order units (longest processing time
+// first): the floating-point form is bound by FP64 throughput and the
+// per-term form by the remainder, both well above the streaming cost.
+double repr_cost(Repr r)
+{
+    switch (r) {
+    case FP64: return 8.0;
+    case PERTERM: return 6.0;
+    default: return 1.0;
+    }
+}
+
+gfp_status build_batch(const gfp_ctx *ctx, const gfp_dot_desc *d, uint64_t count, HostBatch &hb)
+{
+    if (count > 0xFFFFFFFFull) return GFP_ERR_INVALID;
+    hb.pairs.resize(count);
+    hb.aux.resize(count);
+    std::vector<double> cost;
+    uint64_t total_units = 0;
+    for (uint64_t j = 0; j < count; ++j) {
+        const gfp_dot_desc &q = d[j];
+        if (q.p < 2) return GFP_ERR_INVALID;
+        if (q.n && (!q.x || !q.y)) return GFP_ERR_INVALID;
+        if ((((uintptr_t)q.x) | ((uintptr_t)q.y)) & 3u) return GFP_ERR_INVALID;
+        Repr r;
+        if (!resolve_repr(ctx, q.repr, q.p, q.n, &r)) return GFP_ERR_UNSUPPORTED;
+        const uint32_t chunk = chunk_for(ctx, q.p, q.n);
+        const uint64_t nu = q.n ? (q.n + chunk - 1) / chunk : 1;
+        if (nu > 0xFFFFFFFFull) return GFP_ERR_INVALID;
+        DevPair &pr = hb.pairs[j];
+        pr.x = q.x;
+        pr.y = q.y;
+        pr.n = q.n;
+        pr.m = make_mod(q.p);
+        pr.k = k_for(r, q.p);
+        hb.aux[j].repr = (uint32_t)r;
+        hb.aux[j].units = (uint32_t)nu;
+        total_units += nu;
+        hb.bytes += q.n * 8;
+    }
+    if (total_units > 0xFFFFFFFFull) return GFP_ERR_INVALID;
+    hb.units.resize(total_units);
+    cost.resize(total_units);
+    uint64_t u = 0;
+    for (uint64_t j = 0; j < count; ++j) {
+        const uint64_t n = d[j].n;
+        const uint32_t chunk = chunk_for(ctx, d[j].p, n);
+        const double c = repr_cost((Repr)hb.aux[j].repr);
+        if (n == 0) {
+            hb.units[u] = DevUnit{0, 0, (uint32_t)j, 0};
+            cost[u++] = 0.0;
+            continue;
+        }
+        for (uint64_t b = 0; b < n; b += chunk) {
+            const uint64_t e = std::min<uint64_t>(n, b + chunk);
+            hb.units[u] = DevUnit{b, e, (uint32_t)j, 0};
+            cost[u++] = c * (double)(e - b);
+        }
+    }
+    // longest processing time first (stable: equal costs keep pair order)
+    std::vector<uint32_t> order(total_units);
+    for (uint64_t i = 0; i < total_units; ++i) order[i] = (uint32_t)i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+    std::vector<DevUnit> sorted(total_units);
+    for (uint64_t i = 0; i < total_units; ++i) sorted[i] = hb.units[order[i]];
+    hb.units.swap(sorted);
+    return GFP_OK;
+}
+
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Device image of a batch: [pairs | aux | units | slots | tickets | ctr].
+struct BatchLayout {
+    size_t pairs, aux, units, slots, tickets, ctr, total;
+    BatchLayout(uint64_t count, uint64_t n_units)
+    {
+        pairs = 0;
+        aux = align256(pairs + count * sizeof(DevPair));
+        units = align256(aux + count * sizeof(DevPairAux));
+        slots = align256(units + n_units * sizeof(DevUnit));
+        tickets = align256(slots + count * sizeof(unsigned long long));
+        ctr = align256(tickets + count * sizeof(uint32_t));
+        total = align256(ctr + 2 * sizeof(uint32_t));
+    }
+};
+
+}  // namespace
+
+struct gfp_batch_plan {
+    gfp_ctx *ctx = nullptr;
+    void *mem = nullptr;
+    uint64_t count = 0, n_units = 0, bytes = 0;
+    const DevPair *pairs = nullptr;
+    const DevPairAux *aux = nullptr;
+    const DevUnit *units = nullptr;
+    BatchScratch sc;
+    int grid = 0;
+};
+
+static gfp_status upload_batch(const HostBatch &hb, void *mem, const BatchLayout &L,
+                               bool zero_scratch, cudaStream_t s)
+{
+    char *base = (char *)mem;
+    const uint64_t count = hb.pairs.size();
+    if (count) {
+        GFP_CUDA_TRY(cudaMemcpyAsync(base + L.pairs, hb.pairs.data(), count * sizeof(DevPair),
+                                     cudaMemcpyHostToDevice, s));
+        GFP_CUDA_TRY(cudaMemcpyAsync(base + L.aux, hb.aux.data(), count * sizeof(DevPairAux),
+                                     cudaMemcpyHostToDevice, s));
+    }
+    if (!hb.units.empty())
+        GFP_CUDA_TRY(cudaMemcpyAsync(base + L.units, hb.units.data(),
+                                     hb.units.size() * sizeof(DevUnit), cudaMemcpyHostToDevice, s));
+    if (zero_scratch) GFP_CUDA_TRY(cudaMemsetAsync(base + L.slots, 0, L.total - L.slots, s));
+    return GFP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+GFP_API const char *gfp_status_string(int st)
+{
+    switch (st) {
+    case GFP_OK: return "GFP_OK";
+    case GFP_PENDING: return "GFP_PENDING";
+    case GFP_ERR_INVALID: return "GFP_ERR_INVALID";
+    case GFP_ERR_RANGE: return "GFP_ERR_RANGE";
+    case GFP_ERR_UNSUPPORTED: return "GFP_ERR_UNSUPPORTED";
+    case GFP_ERR_NOMEM: return "GFP_ERR_NOMEM";
+    case GFP_ERR_CUDA: return "GFP_ERR_CUDA";
+    case GFP_ERR_AGAIN: return "GFP_ERR_AGAIN";
+    case GFP_ERR_TIMEOUT: return "GFP_ERR_TIMEOUT";
+    case GFP_ERR_UNKNOWN_TICKET: return "GFP_ERR_UNKNOWN_TICKET";
+    case GFP_ERR_CANCELLED: return "GFP_ERR_CANCELLED";
+    default: return "GFP_UNKNOWN_STATUS";
+    }
+}
+
+GFP_API uint64_t gfp_delay_bound(uint32_t p, int acc_bits, int carried)
+{
+    return delay_bound(p, acc_bits, carried);
+}
+
+GFP_API gfp_status gfp_get_params(uint32_t p, gfp_params *out)
+{
+    if (p < 2 || !out) return GFP_ERR_INVALID;
+    const Mod m = make_mod(p);
+    out->p = p;
+    out->corr = m.corr;
+    out->k_u64 = delay_bound(p, 64, 1);
+    out->k_fp64 = delay_bound(p, 53, 1);
+    out->barrett_mu = m.mu;
+    out->inv_p = m.invp;
+    out->fp64_ok = out->k_fp64 >= 1;
+    return GFP_OK;
+}
+
+GFP_API uint32_t gfp_reduce_u64(uint64_t x, uint32_t p)
+{
+    if (p < 2) return 0;
+    return reduce64(x, make_mod(p));
+}
+
+GFP_API double gfp_reduce_f64(double T, uint32_t p)
+{
+    if (p < 2) return 0.0;
+    return reduce_f64(T, make_mod(p));
+}
+
+GFP_API gfp_repr gfp_choose_repr(const gfp_ctx *ctx, uint32_t p, uint64_t n)
+{
+    Repr r;
+    if (p < 2 || !resolve_repr(ctx, GFP_REPR_AUTO, p, n, &r)) return GFP_REPR_AUTO;
+    return (gfp_repr)r;
+}
+
+GFP_API gfp_status gfp_plan_load(gfp_ctx *ctx, const char *path);   // gfp_tune.cu
+
+GFP_API gfp_status gfp_context_create(int device, gfp_ctx **out)
+{
+    if (!out) return GFP_ERR_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return GFP_ERR_CUDA;
+    GFP_CUDA_TRY(cudaSetDevice(device));
+    gfp_ctx *c = new (std::nothrow) gfp_ctx();
+    if (!c) return GFP_ERR_NOMEM;
+    c->device = device;
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) !=
+        cudaSuccess) {
+        delete c;
+        return GFP_ERR_CUDA;
+    }
+    const size_t ring_bytes = (size_t)c->ring_size * (sizeof(unsigned long long) + 4);
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, ring_bytes + 256) != cudaSuccess) {
+        delete c;
+        return GFP_ERR_NOMEM;
+    }
+    cudaMemset(mem, 0, ring_bytes + 256);
+    c->ring_slots = (unsigned long long *)mem;
+    c->ring_tickets = (uint32_t *)((char *)mem + (size_t)c->ring_size * 8);
+    c->d_flag = (uint32_t *)((char *)mem + ring_bytes);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaFree(mem);
+        delete c;
+        return GFP_ERR_CUDA;
+    }
+    if (const char *e = getenv("GFP_FORCE_REPR")) {
+        int r = atoi(e);
+        if (r >= 0 && r < GFP_REPR_COUNT_) c->forced = (gfp_repr)r;
+    }
+    if (const char *e = getenv("GFP_VALIDATE")) c->validate = atoi(e) != 0;
+    if (const char *e = getenv("GFP_PLAN_FILE")) gfp_plan_load(c, e);
+    *out = c;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_context_destroy(gfp_ctx *ctx)
+{
+    if (!ctx) return GFP_ERR_INVALID;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    cudaFree(ctx->ring_slots);
+    if (ctx->bw) cudaFree(ctx->bw);
+    if (ctx->stage) cudaFree(ctx->stage);
+    if (ctx->stage_out) cudaFree(ctx->stage_out);
+    delete ctx;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_set_repr(gfp_ctx *ctx, gfp_repr repr)
+{
+    if (!ctx || repr < GFP_REPR_AUTO || repr >= GFP_REPR_COUNT_) return GFP_ERR_INVALID;
+    ctx->forced = repr;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_set_validate(gfp_ctx *ctx, int on)
+{
+    if (!ctx) return GFP_ERR_INVALID;
+    ctx->validate = on != 0;
+    return GFP_OK;
+}
+
+GFP_API uint64_t gfp_launch_count(const gfp_ctx *ctx) { return ctx ? ctx->launches.load() : 0; }
+
+GFP_API gfp_status gfp_dot(gfp_ctx *ctx, uint32_t p, uint64_t n, const uint32_t *x,
+                           const uint32_t *y, uint32_t *out, void *stream)
+{
+    if (!ctx || p < 2 || !out || (n && (!x || !y))) return GFP_ERR_INVALID;
+    if ((((uintptr_t)x) | ((uintptr_t)y) | ((uintptr_t)out)) & 3u) return GFP_ERR_INVALID;
+    Repr r;
+    if (!resolve_repr(ctx, GFP_REPR_AUTO, p, n, &r)) return GFP_ERR_UNSUPPORTED;
+    cudaStream_t s = as_stream(stream);
+    if (ctx->validate) {
+        gfp_status st = check_range(ctx, x, n, p, s);
+        if (st == GFP_OK) st = check_range(ctx, y, n, p, s);
+        if (st != GFP_OK) return st;
+    }
+    const uint32_t slot = ctx->ring_pos.fetch_add(1) % ctx->ring_size;
+    const int grid = dot_single_grid(r, n, ctx->sm_count);
+    GFP_CUDA_TRY(launch_dot_single(r, make_mod(p), k_for(r, p), n, x, y, ctx->ring_slots + slot,
+                                   ctx->ring_tickets + slot, out, grid, s));
+    ctx->launches++;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_batch_plan_create(gfp_ctx *ctx, const gfp_dot_desc *d, uint64_t count,
+                                         gfp_batch_plan **out)
+{
+    if (!ctx || !out || (count && !d)) return GFP_ERR_INVALID;
+    *out = nullptr;
+    HostBatch hb;
+    gfp_status st = build_batch(ctx, d, count, hb);
+    if (st != GFP_OK) return st;
+    BatchLayout L(count, hb.units.size());
+    gfp_batch_plan *pl = new (std::nothrow) gfp_batch_plan();
+    if (!pl) return GFP_ERR_NOMEM;
+    if (cudaMalloc(&pl->mem, L.total) != cudaSuccess) {
+        delete pl;
+        return GFP_ERR_NOMEM;
+    }
+    st = upload_batch(hb, pl->mem, L, true, 0);
+    if (st == GFP_OK && cudaDeviceSynchronize() != cudaSuccess) st = GFP_ERR_CUDA;
+    if (st != GFP_OK) {
+        cudaFree(pl->mem);
+        delete pl;
+        return st;
+    }
+    char *base = (char *)pl->mem;
+    pl->ctx = ctx;
+    pl->count = count;
+    pl->n_units = hb.units.size();
+    pl->bytes = hb.bytes;
+    pl->pairs = (const DevPair *)(base + L.pairs);
+    pl->aux = (const DevPairAux *)(base + L.aux);
+    pl->units = (const DevUnit *)(base + L.units);
+    pl->sc.slots = (unsigned long long *)(base + L.slots);
+    pl->sc.tickets = (uint32_t *)(base + L.tickets);
+    pl->sc.ctr = (uint32_t *)(base + L.ctr);
+    pl->grid = dot_batched_grid(ctx->sm_count);
+    *out = pl;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_batch_plan_exec(gfp_batch_plan *pl, uint32_t *out, void *stream)
+{
+    if (!pl || (pl->count && !out)) return GFP_ERR_INVALID;
+    if (pl->count == 0) return GFP_OK;
+    GFP_CUDA_TRY(launch_dot_batched(pl->pairs, pl->aux, pl->units, (uint32_t)pl->n_units, pl->sc,
+                                    out, pl->grid, as_stream(stream)));
+    pl->ctx->launches++;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_batch_plan_info(const gfp_batch_plan *pl, uint64_t *units, uint64_t *bytes)
+{
+    if (!pl) return GFP_ERR_INVALID;
+    if (units) *units = pl->n_units;
+    if (bytes) *bytes = pl->bytes;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_batch_plan_destroy(gfp_batch_plan *pl)
+{
+    if (!pl) return GFP_ERR_INVALID;
+    cudaFree(pl->mem);
+    delete pl;
+    return GFP_OK;
+}
+
+static gfp_status batched_oneshot(gfp_ctx *ctx, const gfp_dot_desc *d, uint64_t count,
+                                  uint32_t *out, cudaStream_t s)
+{
+    HostBatch hb;
+    gfp_status st = build_batch(ctx, d, count, hb);
+    if (st != GFP_OK) return st;
+    if (ctx->validate)
+        for (uint64_t j = 0; j < count; ++j) {
+            st = check_range(ctx, d[j].x, d[j].n, d[j].p, s);
+            if (st == GFP_OK) st = check_range(ctx, d[j].y, d[j].n, d[j].p, s);
+            if (st != GFP_OK) return st;
+        }
+    BatchLayout L(count, hb.units.size());
+    bool fresh = false;
+    if (L.total > ctx->bw_bytes) {
+        if (ctx->bw) {
+            GFP_CUDA_TRY(cudaStreamSynchronize(s));
+            cudaFree(ctx->bw);
+            ctx->bw = nullptr;
+            ctx->bw_bytes = 0;
+        }
+        const size_t want = std::max<size_t>(L.total, (size_t)1 << 20);
+        if (cudaMalloc(&ctx->bw, want) != cudaSuccess) return GFP_ERR_NOMEM;
+        ctx->bw_bytes = want;
+        fresh = true;
+    }
+    // the scratch region moves with the layout: clear it whenever it may hold
+    // stale values (fresh buffer, or a layout with a different offset)
+    const bool zero = fresh || ctx->bw_slots_off != L.slots;
+    st = upload_batch(hb, ctx->bw, L, false, s);
+    if (st != GFP_OK) return st;
+    char *base = (char *)ctx->bw;
+    if (zero) GFP_CUDA_TRY(cudaMemsetAsync(base + L.slots, 0, ctx->bw_bytes - L.slots, s));
+    ctx->bw_slots_off = L.slots;
+    BatchScratch sc;
+    sc.slots = (unsigned long long *)(base + L.slots);
+    sc.tickets = (uint32_t *)(base + L.tickets);
+    sc.ctr = (uint32_t *)(base + L.ctr);
+    GFP_CUDA_TRY(launch_dot_batched((const DevPair *)(base + L.pairs),
+                                    (const DevPairAux *)(base + L.aux),
+                                    (const DevUnit *)(base + L.units), (uint32_t)hb.units.size(),
+                                    sc, out, dot_batched_grid(ctx->sm_count), s));
+    ctx->launches++;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_dot_batched(gfp_ctx *ctx, const gfp_dot_desc *d, uint64_t count,
+                                   uint32_t *out, void *stream)
+{
+    if (!ctx || (count && (!d || !out))) return GFP_ERR_INVALID;
+    if (count == 0) return GFP_OK;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    return batched_oneshot(ctx, d, count, out, as_stream(stream));
+}
+
+GFP_API gfp_status gfp_dot_batched_host(gfp_ctx *ctx, uint64_t count, const uint32_t *p,
+                                        const uint64_t *n, const uint64_t *off,
+                                        const uint32_t *x_host, const uint32_t *y_host,
+                                        uint64_t total, uint32_t *out_host, void *stream)
+{
+    if (!ctx || (count && (!p || !n || !off || !out_host))) return GFP_ERR_INVALID;
+    if (count == 0) return GFP_OK;
+    if (total && (!x_host || !y_host)) return GFP_ERR_INVALID;
+    for (uint64_t j = 0; j < count; ++j)
+        if ((off[j] & 3u) || off[j] > total || n[j] > total - off[j] || p[j] < 2)
+            return GFP_ERR_INVALID;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    cudaStream_t s = as_stream(stream);
+    const size_t need = (size_t)2 * (total ? total : 1);
+    if (need > ctx->stage_elems) {
+        GFP_CUDA_TRY(cudaStreamSynchronize(s));
+        if (ctx->stage) cudaFree(ctx->stage);
+        ctx->stage = nullptr;
+        ctx->stage_elems = 0;
+        if (cudaMalloc(&ctx->stage, need * 4) != cudaSuccess) return GFP_ERR_NOMEM;
+        ctx->stage_elems = need;
+    }
+    if (count > ctx->stage_out_elems) {
+        GFP_CUDA_TRY(cudaStreamSynchronize(s));
+        if (ctx->stage_out) cudaFree(ctx->stage_out);
+        ctx->stage_out = nullptr;
+        ctx->stage_out_elems = 0;
+        if (cudaMalloc(&ctx->stage_out, count * 4) != cudaSuccess) return GFP_ERR_NOMEM;
+        ctx->stage_out_elems = count;
+    }
+    uint32_t *dx = ctx->stage, *dy = ctx->stage + (total ? total : 1);
+    if (total) {
+        GFP_CUDA_TRY(cudaMemcpyAsync(dx, x_host, total * 4, cudaMemcpyHostToDevice, s));
+        GFP_CUDA_TRY(cudaMemcpyAsync(dy, y_host, total * 4, cudaMemcpyHostToDevice, s));
+    }
+    std::vector<gfp_dot_desc> d(count);
+    for (uint64_t j = 0; j < count; ++j)
+        d[j] = gfp_dot_desc{p[j], GFP_REPR_AUTO, n[j], dx + off[j], dy + off[j]};
+    gfp_status st = batched_oneshot(ctx, d.data(), count, ctx->stage_out, s);
+    if (st != GFP_OK) return st;
+    GFP_CUDA_TRY(cudaMemcpyAsync(out_host, ctx->stage_out, count * 4, cudaMemcpyDeviceToHost, s));
+    GFP_CUDA_TRY(cudaStreamSynchronize(s));
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_matvec(gfp_ctx *ctx, uint32_t p, uint64_t rows, uint64_t cols,
+                              const uint32_t *A, uint64_t lda, const uint32_t *x, uint32_t *y,
+                              void *stream)
+{
+    if (!ctx || p < 2 || lda < cols || (rows && !y) || (rows && cols && (!A || !x)))
+        return GFP_ERR_INVALID;
+    if ((((uintptr_t)A) | ((uintptr_t)x) | ((uintptr_t)y)) & 3u) return GFP_ERR_INVALID;
+    if (rows == 0) return GFP_OK;
+    Repr r;
+    if (!resolve_repr(ctx, GFP_REPR_AUTO, p, cols, &r)) return GFP_ERR_UNSUPPORTED;
+    cudaStream_t s = as_stream(stream);
+    if (ctx->validate) {
+        gfp_status st = check_range(ctx, x, cols, p, s);
+        for (uint64_t i = 0; st == GFP_OK && i < rows; ++i) st = check_range(ctx, A + i * lda, cols, p, s);
+        if (st != GFP_OK) return st;
+    }
+    GFP_CUDA_TRY(launch_matvec(r, make_mod(p), k_for(r, p), rows, cols, A, lda, x, y,
+                               ctx->sm_count, s));
+    ctx->launches++;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_matvec_iterate(gfp_ctx *ctx, uint32_t p, uint64_t n, const uint32_t *A,
+                                      uint64_t lda, const uint32_t *x0, uint32_t *Y,
+                                      uint32_t iters, void *stream)
+{
+    if (!ctx || p < 2 || lda < n || (n && (!A || !x0 || !Y))) return GFP_ERR_INVALID;
+    if ((((uintptr_t)A) | ((uintptr_t)x0) | ((uintptr_t)Y)) & 3u) return GFP_ERR_INVALID;
+    if (n == 0 || iters == 0) return GFP_OK;
+    Repr r;
+    if (!resolve_repr(ctx, GFP_REPR_AUTO, p, n, &r)) return GFP_ERR_UNSUPPORTED;
+    cudaStream_t s = as_stream(stream);
+    std::lock_guard<std::mutex> g(ctx->mu);
+    gfp_ctx::GraphKey key{p, n, A, lda, x0, Y, iters, (int)r};
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        // warm the launch path (function attributes) outside capture
+        cudaStream_t cs;
+        GFP_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        const Mod m = make_mod(p);
+        const uint64_t k = k_for(r, p);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        for (uint32_t t = 0; e == cudaSuccess && t < iters; ++t) {
+            const uint32_t *xt = t ? Y + (uint64_t)(t - 1) * n : x0;
+            e = launch_matvec(r, m, k, n, n, A, lda, xt, Y + (uint64_t)t * n, ctx->sm_count, cs);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e2;
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return GFP_ERR_CUDA;
+        it = ctx->graphs.emplace(key, exec).first;
+    }
+    GFP_CUDA_TRY(cudaGraphLaunch(it->second, s));
+    ctx->launches += iters;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_fill_uniform(uint32_t p, uint64_t seed, uint64_t stream_id,
+                                    uint64_t offset, uint64_t n, uint32_t *out, void *stream)
+{
+    if (p < 2 || (n && !out)) return GFP_ERR_INVALID;
+    GFP_CUDA_TRY(launch_fill_uniform(p, seed, stream_id, offset, n, out, as_stream(stream)));
+    return GFP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,393 @@
+"""Python binding of libgfpdot (ctypes): argument marshalling only.
+
+Every function keeps the name of the C entry point it calls (declared in
+``include/gfpdot.h``).  Device operands are torch CUDA tensors of dtype
+uint32 (or int32 holding the same bits); the current torch stream is used
+unless ``stream`` is given.  A non-OK status raises :class:`GfpError`.  There
+is no fallback: if the shared library is missing, importing the functions
+raises, and every computation runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+GFP_OK = 0
+GFP_PENDING = 1
+GFP_ERR_INVALID = -1
+GFP_ERR_RANGE = -2
+GFP_ERR_UNSUPPORTED = -3
+GFP_ERR_NOMEM = -4
+GFP_ERR_CUDA = -5
+GFP_ERR_AGAIN = -6
+GFP_ERR_TIMEOUT = -7
+GFP_ERR_UNKNOWN_TICKET = -8
+GFP_ERR_CANCELLED = -9
+
+GFP_REPR_AUTO = 0
+GFP_REPR_PERTERM = 1
+GFP_REPR_U64_BLOCK = 2
+GFP_REPR_U64_CARRY = 3
+GFP_REPR_FP64 = 4
+REPR_NAMES = {0: "auto", 1: "perterm", 2: "u64_block", 3: "u64_carry", 4: "fp64"}
+
+_vp = ctypes.c_void_p
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+_int = ctypes.c_int
+
+
+class GfpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {gfp_status_string(status)} ({status})")
+
+
+class gfp_params(ctypes.Structure):
+    _fields_ = [("p", _u32), ("corr", _u32), ("k_u64", _u64), ("k_fp64", _u64),
+                ("barrett_mu", _u64), ("inv_p", ctypes.c_double), ("fp64_ok", _int)]
+
+
+class gfp_dot_desc(ctypes.Structure):
+    _fields_ = [("p", _u32), ("repr", _u32), ("n", _u64), ("x", _vp), ("y", _vp)]
+
+
+_SIGS = {
+    "gfp_status_string": (ctypes.c_char_p, [_int]),
+    "gfp_delay_bound": (_u64, [_u32, _int, _int]),
+    "gfp_get_params": (_int, [_u32, ctypes.POINTER(gfp_params)]),
+    "gfp_reduce_u64": (_u32, [_u64, _u32]),
+    "gfp_reduce_f64": (ctypes.c_double, [ctypes.c_double, _u32]),
+    "gfp_choose_repr": (_int, [_vp, _u32, _u64]),
+    "gfp_context_create": (_int, [_int, ctypes.POINTER(_vp)]),
+    "gfp_context_destroy": (_int, [_vp]),
+    "gfp_set_repr": (_int, [_vp, _int]),
+    "gfp_set_validate": (_int, [_vp, _int]),
+    "gfp_launch_count": (_u64, [_vp]),
+    "gfp_dot": (_int, [_vp, _u32, _u64, _vp, _vp, _vp, _vp]),
+    "gfp_dot_batched": (_int, [_vp, ctypes.POINTER(gfp_dot_desc), _u64, _vp, _vp]),
+    "gfp_batch_plan_create": (_int, [_vp, ctypes.POINTER(gfp_dot_desc), _u64, ctypes.POINTER(_vp)]),
+    "gfp_batch_plan_exec": (_int, [_vp, _vp, _vp]),
+    "gfp_batch_plan_info": (_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    "gfp_batch_plan_destroy": (_int, [_vp]),
+    "gfp_dot_batched_host": (_int, [_vp, _u64, _vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp]),
+    "gfp_matvec": (_int, [_vp, _u32, _u64, _u64, _vp, _u64, _vp, _vp, _vp]),
+    "gfp_matvec_iterate": (_int, [_vp, _u32, _u64, _vp, _u64, _vp, _vp, _u32, _vp]),
+    "gfp_tune": (_int, [_vp, _vp, _u32, _u32, _u32, ctypes.c_char_p]),
+    "gfp_plan_load": (_int, [_vp, ctypes.c_char_p]),
+    "gfp_plan_save": (_int, [_vp, ctypes.c_char_p]),
+    "gfp_plan_size": (_u64, [_vp]),
+    "gfp_fill_uniform": (_int, [_u32, _u64, _u64, _u64, _u64, _vp, _vp]),
+}
+
+_lib = None
+
+
+def load(auto_build: bool = True):
+    """Load the in-tree libgfpdot.so (building it first when stale)."""
+    global _lib
+    if _lib is None:
+        if auto_build:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libgfpdot.so is missing at {_build.LIB}: build it with "
+                               "paper_cs_0404008_gb300.build.build()")
+        lib = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def declared_symbols() -> list[str]:
+    return sorted(_SIGS)
+
+
+def _check(st: int, where: str):
+    if st != GFP_OK:
+        raise GfpError(st, where)
+
+
+def _ptr(t) -> int:
+    """Device (or host) address of a tensor / numpy array / int."""
+    if t is None:
+        return 0
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):
+        return t.ctypes.data
+    raise TypeError(f"cannot take the address of {type(t)}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check_u32(t, n: int, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype not in (torch.uint32, torch.int32):
+        raise TypeError(f"{name} must be uint32 (or int32 bit-identical), got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < n:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {n}")
+
+
+# ---- host-only functions ----
+
+def gfp_status_string(st: int) -> str:
+    return load().gfp_status_string(st).decode()
+
+
+def gfp_delay_bound(p: int, acc_bits: int, carried: int) -> int:
+    return int(load().gfp_delay_bound(p, acc_bits, carried))
+
+
+def gfp_get_params(p: int) -> dict:
+    out = gfp_params()
+    _check(load().gfp_get_params(p, ctypes.byref(out)), "gfp_get_params")
+    return {f: getattr(out, f) for f, _ in gfp_params._fields_}
+
+
+def gfp_reduce_u64(x: int, p: int) -> int:
+    return int(load().gfp_reduce_u64(x, p))
+
+
+def gfp_reduce_f64(T: float, p: int) -> float:
+    return float(load().gfp_reduce_f64(T, p))
+
+
+def gfp_choose_repr(ctx, p: int, n: int) -> int:
+    return int(load().gfp_choose_repr(ctx.handle if ctx else None, p, n))
+
+
+# ---- context ----
+
+class Context:
+    """Owns a gfp_ctx handle bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        torch.cuda.init()
+        h = _vp()
+        _check(load().gfp_context_create(device, ctypes.byref(h)), "gfp_context_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            _check(load().gfp_context_destroy(self.handle), "gfp_context_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_repr(self, repr_: int):
+        _check(load().gfp_set_repr(self.handle, repr_), "gfp_set_repr")
+
+    def set_validate(self, on: bool):
+        _check(load().gfp_set_validate(self.handle, int(bool(on))), "gfp_set_validate")
+
+    def launch_count(self) -> int:
+        return int(load().gfp_launch_count(self.handle))
+
+
+def gfp_context_create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def gfp_context_destroy(ctx: Context):
+    ctx.close()
+
+
+def gfp_set_repr(ctx: Context, repr_: int):
+    ctx.set_repr(repr_)
+
+
+def gfp_set_validate(ctx: Context, on: bool):
+    ctx.set_validate(on)
+
+
+def gfp_launch_count(ctx: Context) -> int:
+    return ctx.launch_count()
+
+
+# ---- dot products ----
+
+def gfp_dot(ctx: Context, p: int, x, y, out, stream=None, n: int | None = None):
+    """out[0] = dot(x[:n], y[:n]) mod p (device tensors)."""
+    n = x.numel() if n is None else n
+    _check_u32(x, n, "x")
+    _check_u32(y, n, "y")
+    _check_u32(out, 1, "out")
+    _check(load().gfp_dot(ctx.handle, p, n, _ptr(x), _ptr(y), _ptr(out), _stream(stream)),
+           "gfp_dot")
+    return out
+
+
+def _descs(pairs):
+    """pairs: iterable of (p, x, y[, n[, repr]]) with x, y device tensors or raw addresses."""
+    pairs = list(pairs)
+    arr = (gfp_dot_desc * max(1, len(pairs)))()
+    for j, t in enumerate(pairs):
+        p, x, y = t[0], t[1], t[2]
+        n = t[3] if len(t) > 3 and t[3] is not None else x.numel()
+        r = t[4] if len(t) > 4 else GFP_REPR_AUTO
+        arr[j].p = p
+        arr[j].repr = r
+        arr[j].n = n
+        arr[j].x = _ptr(x)
+        arr[j].y = _ptr(y)
+    return arr, len(pairs)
+
+
+def gfp_dot_batched(ctx: Context, pairs, out, stream=None):
+    arr, count = _descs(pairs)
+    if count:
+        _check_u32(out, count, "out")
+    _check(load().gfp_dot_batched(ctx.handle, arr, count, _ptr(out), _stream(stream)),
+           "gfp_dot_batched")
+    return out
+
+
+class BatchPlan:
+    """gfp_batch_plan: device-resident work list, one launch per exec."""
+
+    def __init__(self, ctx: Context, pairs):
+        arr, count = _descs(pairs)
+        h = _vp()
+        _check(load().gfp_batch_plan_create(ctx.handle, arr, count, ctypes.byref(h)),
+               "gfp_batch_plan_create")
+        self.handle = h
+        self.count = count
+        self._keep = pairs  # keep operand tensors alive with the plan
+
+    def exec(self, out, stream=None):
+        _check_u32(out, self.count, "out")
+        _check(load().gfp_batch_plan_exec(self.handle, _ptr(out), _stream(stream)),
+               "gfp_batch_plan_exec")
+        return out
+
+    def info(self):
+        u, b = _u64(), _u64()
+        _check(load().gfp_batch_plan_info(self.handle, ctypes.byref(u), ctypes.byref(b)),
+               "gfp_batch_plan_info")
+        return int(u.value), int(b.value)
+
+    def close(self):
+        if self.handle:
+            load().gfp_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gfp_batch_plan_create(ctx: Context, pairs) -> BatchPlan:
+    return BatchPlan(ctx, pairs)
+
+
+def gfp_batch_plan_exec(plan: BatchPlan, out, stream=None):
+    return plan.exec(out, stream)
+
+
+def gfp_batch_plan_destroy(plan: BatchPlan):
+    plan.close()
+
+
+def gfp_dot_batched_host(ctx: Context, ps, ns, offs, x_host, y_host, out_host, stream=None):
+    """Host-buffer batch (numpy or pinned CPU tensors); synchronous."""
+    import numpy as np
+    ps = np.ascontiguousarray(ps, dtype=np.uint32)
+    ns = np.ascontiguousarray(ns, dtype=np.uint64)
+    offs = np.ascontiguousarray(offs, dtype=np.uint64)
+    total = int(x_host.numel() if hasattr(x_host, "numel") else x_host.shape[0])
+    _check(load().gfp_dot_batched_host(ctx.handle, ps.shape[0], ps.ctypes.data, ns.ctypes.data,
+                                       offs.ctypes.data, _ptr(x_host), _ptr(y_host), total,
+                                       _ptr(out_host), _stream(stream)),
+           "gfp_dot_batched_host")
+    return out_host
+
+
+# ---- matrix-vector ----
+
+def gfp_matvec(ctx: Context, p: int, A, x, y, stream=None, lda: int | None = None,
+               rows: int | None = None, cols: int | None = None):
+    rows = A.shape[0] if rows is None else rows
+    cols = A.shape[1] if cols is None else cols
+    lda = A.stride(0) if lda is None else lda
+    _check_u32(x, cols, "x")
+    _check_u32(y, rows, "y")
+    _check(load().gfp_matvec(ctx.handle, p, rows, cols, _ptr(A), lda, _ptr(x), _ptr(y),
+                             _stream(stream)), "gfp_matvec")
+    return y
+
+
+def gfp_matvec_iterate(ctx: Context, p: int, A, x0, Y, iters: int, stream=None,
+                       lda: int | None = None):
+    n = A.shape[0]
+    lda = A.stride(0) if lda is None else lda
+    _check_u32(x0, n, "x0")
+    _check_u32(Y, n * iters, "Y")
+    _check(load().gfp_matvec_iterate(ctx.handle, p, n, _ptr(A), lda, _ptr(x0), _ptr(Y), iters,
+                                     _stream(stream)), "gfp_matvec_iterate")
+    return Y
+
+
+# ---- tuning ----
+
+def gfp_tune(ctx: Context, primes=None, lg_lo: int = 8, lg_hi: int = 20,
+             plan_path: str | None = None):
+    import numpy as np
+    arr = None if primes is None else np.ascontiguousarray(primes, dtype=np.uint32)
+    _check(load().gfp_tune(ctx.handle, None if arr is None else arr.ctypes.data,
+                           0 if arr is None else arr.shape[0], lg_lo, lg_hi,
+                           plan_path.encode() if plan_path else None), "gfp_tune")
+
+
+def gfp_plan_load(ctx: Context, path: str):
+    _check(load().gfp_plan_load(ctx.handle, path.encode()), "gfp_plan_load")
+
+
+def gfp_plan_save(ctx: Context, path: str):
+    _check(load().gfp_plan_save(ctx.handle, path.encode()), "gfp_plan_save")
+
+
+def gfp_plan_size(ctx: Context) -> int:
+    return int(load().gfp_plan_size(ctx.handle))
+
+
+# ---- synthetic inputs ----
+
+def gfp_fill_uniform(p: int, seed: int, stream_id: int, out, n: int | None = None,
+                     offset: int = 0, stream=None):
+    n = out.numel() if n is None else n
+    _check_u32(out, n, "out")
+    _check(load().gfp_fill_uniform(p, seed, stream_id, offset, n, _ptr(out), _stream(stream)),
+           "gfp_fill_uniform")
+    return out

@@ -1,0 +1,59 @@
+"""The C-ABI library loads without a GPU and exports every declared symbol."""
+import ctypes
+import os
+import re
+import subprocess
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "gfpdot.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"GFP_API\s+[\w\s\*]+?\b(gfp_\w+)\s*\(", txt)))
+
+
+def test_header_symbols_exported(lib):
+    syms = header_symbols()
+    assert len(syms) >= 20
+    so = ctypes.CDLL(lib.lib_path())
+    missing = [s for s in syms if not hasattr(so, s)]
+    assert not missing, missing
+
+
+def test_binding_covers_header(lib):
+    assert set(header_symbols()) <= set(lib.declared_symbols()) | {"gfp_get_params"}
+
+
+def test_exports_are_only_the_abi(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.lib_path()], capture_output=True,
+                         text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    ours = {s for s in exported if s.startswith("gfp_")}
+    assert ours == set(header_symbols())
+
+
+def test_status_strings(lib):
+    assert lib.gfp_status_string(0) == "GFP_OK"
+    assert lib.gfp_status_string(-2) == "GFP_ERR_RANGE"
+    assert lib.gfp_status_string(12345) == "GFP_UNKNOWN_STATUS"
+
+
+def test_choose_repr_rules_without_context(lib):
+    assert lib.gfp_choose_repr(None, 65521, 1 << 20) == lib.GFP_REPR_U64_BLOCK
+    assert lib.gfp_choose_repr(None, 2147483647, 1 << 20) == lib.GFP_REPR_U64_CARRY
+    assert lib.gfp_choose_repr(None, 4294967291, 10) == lib.GFP_REPR_U64_CARRY
+    assert lib.gfp_choose_repr(None, 1, 10) == lib.GFP_REPR_AUTO
+
+
+def test_no_oracle_in_product():
+    """The library and its binding never reference the oracle."""
+    pkg = os.path.join(ROOT, "paper_cs_0404008_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "gfp_oracle" not in txt and "liboracle" not in txt, f
