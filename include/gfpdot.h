@@ -188,6 +188,25 @@ GFP_API gfp_status gfp_dot_batched_host(gfp_ctx *ctx, uint64_t count, const uint
                                         const uint32_t *x_host, const uint32_t *y_host,
                                         uint64_t total, uint32_t *out_host, void *stream);
 
+/* Batched dot products that allocate nothing (no counterpart in the paper:
+ * an interface convenience).  For callers that cannot call cudaMalloc where
+ * they need the result (fixed device-memory budgets owned by a host
+ * application, paths where an allocation may block or fail): same result
+ * and same kernel as gfp_dot_batched, but all scratch lives in one
+ * file-scope device array of fixed size that every device loading the
+ * library holds until process exit.  No context is needed; the current CUDA
+ * device is used and GFP_REPR_AUTO follows the built-in rules.
+ *   d: host array of count descriptors (operands on the current device).
+ *   out: device, count uint32_t.
+ * Limits: count <= 1024 pairs and at most 16384 work units of 65536
+ * elements (about 2^30 elements in total); beyond either, GFP_ERR_INVALID
+ * with nothing enqueued.  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the array (each clears the parts that must start at zero): calls
+ * whose work overlaps on the GPU race, so order them on one stream. */
+GFP_API gfp_status gfp_dot_batched_noalloc(const gfp_dot_desc *d, uint64_t count, uint32_t *out,
+                                           void *stream);
+
 /* ---- matrix-vector (the iterative use named in Section 1) ---- */
 
 /* y[i] = (sum_j A[i*lda + j] * x[j]) mod p for 0 <= i < rows.

@@ -72,6 +72,7 @@ _SIGS = {
     "gfp_batch_plan_exec": (_int, [_vp, _vp, _vp]),
     "gfp_batch_plan_info": (_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "gfp_batch_plan_destroy": (_int, [_vp]),
+    "gfp_dot_batched_noalloc": (_int, [ctypes.POINTER(gfp_dot_desc), _u64, _vp, _vp]),
     "gfp_dot_batched_host": (_int, [_vp, _u64, _vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp]),
     "gfp_matvec": (_int, [_vp, _u32, _u64, _u64, _vp, _u64, _vp, _vp, _vp]),
     "gfp_matvec_iterate": (_int, [_vp, _u32, _u64, _vp, _u64, _vp, _vp, _u32, _vp]),
@@ -269,6 +270,17 @@ def gfp_dot_batched(ctx: Context, pairs, out, stream=None):
         _check_u32(out, count, "out")
     _check(load().gfp_dot_batched(ctx.handle, arr, count, _ptr(out), _stream(stream)),
            "gfp_dot_batched")
+    return out
+
+
+def gfp_dot_batched_noalloc(pairs, out, stream=None):
+    """Batched dot products using the library's fixed device scratch array
+    (no allocation anywhere; at most 1024 pairs, see the header)."""
+    arr, count = _descs(pairs)
+    if count:
+        _check_u32(out, count, "out")
+    _check(load().gfp_dot_batched_noalloc(arr, count, _ptr(out), _stream(stream)),
+           "gfp_dot_batched_noalloc")
     return out
 
 
