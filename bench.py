@@ -252,11 +252,13 @@ def run_gpu(args):
 
     # --- autotune (install-time selection, per (p, n) bucket) ---
     t_tune = time.perf_counter()
-    g.gfp_tune(ctx, list(gi.PRIMES_BATCHED), 8, 20, None)
+    if not args.no_tune:
+        g.gfp_tune(ctx, list(gi.PRIMES_BATCHED), 8, 20, None)
     t_tune = time.perf_counter() - t_tune
 
-    batch = Batch(g, torch, SEED + 1000 * rank)
-    out = torch.empty(COUNT, dtype=torch.int32, device="cuda")
+    count = args.pairs
+    batch = Batch(g, torch, SEED + 1000 * rank, count)
+    out = torch.empty(count, dtype=torch.int32, device="cuda")
     plan = g.BatchPlan(ctx, batch.pairs())
     n_units, _ = plan.info()
 
@@ -267,7 +269,7 @@ def run_gpu(args):
     sampler = ClockSampler(dev_index)
     sampler.start()
     t_load = time.time()
-    while time.time() - t_load < 1.0:
+    while not args.no_clocks and time.time() - t_load < 1.0:
         for _ in range(50):
             plan.exec(out, stream)
         torch.cuda.synchronize()
@@ -314,7 +316,7 @@ def run_gpu(args):
         yh = torch.empty(batch.total, dtype=torch.int32, pin_memory=True)
         xh.copy_(batch.x)
         yh.copy_(batch.y)
-        oh = torch.empty(COUNT, dtype=torch.int32, pin_memory=True)
+        oh = torch.empty(count, dtype=torch.int32, pin_memory=True)
         lens_u = batch.lens.astype(np.uint64)
         offs_u = batch.off.astype(np.uint64)
         ps_u = batch.ps.astype(np.uint32)
@@ -327,7 +329,7 @@ def run_gpu(args):
         barrier()
         dt = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": batch.macs * world * e2e_steps / dt / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": int(2 * 4 * batch.total), "d2h_bytes_per_step": int(4 * COUNT)}
+               "h2d_bytes_per_step": int(2 * 4 * batch.total), "d2h_bytes_per_step": int(4 * count)}
         # results of the e2e path equal the device path
         torch.cuda.synchronize()
         if not np.array_equal(oh.numpy().view(np.uint32), out.cpu().numpy().view(np.uint32)):
@@ -343,16 +345,21 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "pairs": COUNT, "macs_per_step": batch.macs,
+            "config": {"workload": WORKLOAD if count == COUNT else WORKLOAD.replace("4096 pairs", f"{count} pairs"),
+                       "pairs": count, "macs_per_step": batch.macs,
                        "operand_bytes_per_step": batch.bytes, "work_units": n_units,
                        "l2": "inputs larger than L2 (operands ~4.1 GB per step)",
                        "parallelism": f"weak: {world} independent batch(es)",
-                       "tune_seconds": round(t_tune, 2)},
+                       "tune_seconds": round(t_tune, 2),
+                       "plan": "built-in rules" if args.no_tune else "tuned at setup"},
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy test)",
                          "kernel": "k_dot_batched",
-                         "traffic": (trec["dram_bytes_per_launch"] if trec else None)},
+                         "traffic": (trec["dram_bytes_per_algorithmic_byte"] * batch.bytes
+                                     if trec else None),
+                         "traffic_source": ("ncu dram bytes of a 512-pair capture, scaled by "
+                                            "algorithmic bytes" if trec else None)},
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -387,6 +394,203 @@ def cpu_baseline():
             "sample": f"every 4th pair of the batch ({len(sel)} pairs, {lens_s.sum():.3e} MACs) x {reps}"}
 
 
+# ---------------------------------------------------------------------------
+# secondary workloads (one JSON line each): single dot, Wiedemann matvec
+# ---------------------------------------------------------------------------
+
+def _events(torch, n):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def run_secondary(args):
+    import torch
+    from paper_cs_0404008_gb300 import gfpdot as g
+
+    torch.cuda.set_device(0)
+    g.load()
+    ctx = g.Context(0)
+    stream = torch.cuda.Stream()
+    peak, peak_kind = hbm_peak()
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic"}
+    if args.workload == "dot":
+        p, n, nvec = 65521, 1 << 20, 256
+        seed = gi.BASE_SEED
+        # 256 operand pairs on rotating buffers: 2 GiB, larger than L2
+        X = torch.empty((nvec, n), dtype=torch.int32, device="cuda")
+        Y = torch.empty((nvec, n), dtype=torch.int32, device="cuda")
+        for i in range(nvec):
+            g.gfp_fill_uniform(p, seed, 2 * i, X[i])
+            g.gfp_fill_uniform(p, seed, 2 * i + 1, Y[i])
+        out = torch.empty(nvec, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        # (i) single-call latency, back to back on one buffer (8 MiB, L2-resident)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                g.gfp_dot(ctx, p, X[0], Y[0], out[0:1], stream)
+            ev = _events(torch, args.steps + 1)
+            ev[0].record(stream)
+            for i in range(args.steps):
+                g.gfp_dot(ctx, p, X[0], Y[0], out[0:1], stream)
+                ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        lat = sorted(ev[i].elapsed_time(ev[i + 1]) * 1e3 for i in range(args.steps))
+        # (ii) 256 dots captured in one CUDA graph, rotating buffers (L2 cold)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            for i in range(nvec):
+                g.gfp_dot(ctx, p, X[i], Y[i], out[i:i + 1], stream)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(graph, stream=stream):
+                for i in range(nvec):
+                    g.gfp_dot(ctx, p, X[i], Y[i], out[i:i + 1], stream)
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch, 2)
+        reps = max(5, args.steps // 20)
+        e0.record()
+        for _ in range(reps):
+            graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        t_graph = e0.elapsed_time(e1) / reps
+        # (iii) the same 256 dots as one persistent batched launch
+        plan = g.BatchPlan(ctx, [(p, X[i], Y[i], n) for i in range(nvec)])
+        ms, per = time_plan(torch, plan, out, max(10, args.steps // 10), stream)
+        t_batch = ms / len(per)
+        macs = float(nvec * n)
+        gm = lambda t_ms: macs / (t_ms / 1e3) / 1e9
+        line.update({
+            "value": gm(t_batch), "ms_per_step": t_batch,
+            "config": {"workload": "256 dot products over GF(65521), n=2^20 each, uint32 uniform "
+                                   "residues on rotating buffers (2 GiB, larger than L2)",
+                       "step": "one persistent batched launch over the 256 pairs"},
+            "single_call_us": {"p50": lat[len(lat) // 2], "p10": lat[len(lat) // 10],
+                               "p90": lat[(9 * len(lat)) // 10]},
+            "graph_of_256_single_dots": {"ms": t_graph, "gmacs": gm(t_graph),
+                                          "gbs": 8 * macs / (t_graph / 1e3) / 1e9},
+            "roofline": {"bound": "hbm", "achieved": 8 * macs / (t_batch / 1e3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": 8 * macs / (t_batch / 1e3) / 1e9 / peak,
+                         "kernel": "k_dot_batched", "traffic": None,
+                         "peak_kind": f"{peak_kind} hbm_gbs"},
+            "gpu_launches": len(per),
+        })
+        plan.close()
+    elif args.workload == "matvec":
+        p, n, iters = 2147483647, 32768, 64
+        A = torch.empty((n, n), dtype=torch.int32, device="cuda")
+        g.gfp_fill_uniform(p, gi.BASE_SEED + 2, 0, A)
+        x0 = torch.empty(n, dtype=torch.int32, device="cuda")
+        g.gfp_fill_uniform(p, gi.BASE_SEED + 2, 1, x0)
+        Y = torch.empty(iters * n, dtype=torch.int32, device="cuda")
+        res = {}
+        for name, rp in (("auto", 0), ("perterm", g.GFP_REPR_PERTERM)):
+            ctx.set_repr(rp)
+            with torch.cuda.stream(stream):
+                for _ in range(2):
+                    g.gfp_matvec_iterate(ctx, p, A, x0, Y, iters, stream)
+                torch.cuda.synchronize()
+                reps = 3 if name == "auto" else 1
+                e0, e1 = _events(torch, 2)
+                e0.record(stream)
+                for _ in range(reps):
+                    g.gfp_matvec_iterate(ctx, p, A, x0, Y, iters, stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            res[name] = e0.elapsed_time(e1) / reps
+        ctx.set_repr(0)
+        macs = float(iters) * n * n
+        t = res["auto"]
+        achieved = 4 * macs / (t / 1e3) / 1e9
+        line.update({
+            "value": macs / (t / 1e3) / 1e9, "ms_per_step": t,
+            "config": {"workload": "Wiedemann iteration over GF(2147483647): A 32768x32768 uint32 "
+                                   "uniform, x_{t+1} = A x_t for 64 iterations in one CUDA graph",
+                       "l2": "A is 4 GiB, larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "kernel": "k_matvec",
+                         "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs"},
+            "same_gpu": {"perterm_ms": res["perterm"],
+                         "perterm_gmacs": macs / (res["perterm"] / 1e3) / 1e9,
+                         "speedup_over_perterm": res["perterm"] / t},
+            "gpu_launches": iters,
+        })
+    elif args.workload in ("block", "csr"):
+        p, m, k, nb = 65521, args.block_m, 16384, 64
+        seed = gi.BASE_SEED + 3
+        B = torch.empty((k, nb), dtype=torch.int32, device="cuda")
+        g.gfp_fill_uniform(p, seed, 1, B)
+        C = torch.empty((m, nb), dtype=torch.int32, device="cuda")
+        macs = float(m) * k * nb
+
+        def timed(fn, reps):
+            with torch.cuda.stream(stream):
+                for _ in range(2):
+                    fn()
+                torch.cuda.synchronize()
+                e0, e1 = _events(torch, 2)
+                e0.record(stream)
+                for _ in range(reps):
+                    fn()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        if args.workload == "block":
+            A = torch.empty((m, k), dtype=torch.int32, device="cuda")
+            g.gfp_fill_uniform(p, seed, 0, A)
+            res = {}
+            for name, rp, reps in (("f16tc", g.GFP_REPR_F16TC, max(10, args.steps // 4)),
+                                   ("u64_block_cuda_core", g.GFP_REPR_U64_BLOCK, 5),
+                                   ("perterm_cuda_core", g.GFP_REPR_PERTERM, 2)):
+                ctx.set_repr(rp)
+                res[name] = timed(lambda: g.gfp_matmul_block(ctx, p, A, B, C, stream), reps)
+            ctx.set_repr(0)
+            assert g.gfp_context_check(ctx) == g.GFP_OK
+            t = res["f16tc"]
+            abytes = 4.0 * m * k + 4.0 * k * nb + 4.0 * m * nb
+            achieved = abytes / (t / 1e3) / 1e9
+            tflops = 4 * 2 * macs / (t / 1e3) / 1e12   # four digit products per multiply-add
+            line.update({
+                "value": macs / (t / 1e3) / 1e9, "ms_per_step": t,
+                "config": {"workload": f"block product over GF(65521): A {m}x{k} times B {k}x{nb}, "
+                                       "uint32 uniform residues, tensor-core path (balanced fp16 digits)",
+                           "l2": "A is larger than L2" if m * k * 4 > (129 << 20) else "A fits L2"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "kernel": "k_block_tc (+k_block_prep_b)",
+                             "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs",
+                             "tensor_tflops_fp16": tflops},
+                "same_gpu": {n: {"ms": v, "gmacs": macs / (v / 1e3) / 1e9} for n, v in res.items()},
+                "gpu_launches": 2,
+            })
+        else:
+            row_ptr, col, val = gi.csr_pattern(m, k, 0.01, p, seed)
+            rp_d = torch.from_numpy(row_ptr.view(np.int32)).cuda()
+            col_d = torch.from_numpy(col.view(np.int32)).cuda()
+            val_d = torch.from_numpy(val.view(np.int32)).cuda()
+            nnz = int(row_ptr[-1])
+            t = timed(lambda: g.gfp_matmul_block_csr(ctx, p, k, rp_d, col_d, val_d, B, C, stream),
+                      max(10, args.steps // 4))
+            cmacs = float(nnz) * nb
+            abytes = 8.0 * nnz + 4.0 * (m + 1) + 4.0 * k * nb + 4.0 * m * nb
+            line.update({
+                "value": cmacs / (t / 1e3) / 1e9, "ms_per_step": t,
+                "config": {"workload": f"sparse-row block product over GF(65521): CSR A {m}x{k} with "
+                                       f"Bernoulli(0.01) rows ({nnz} nonzeros) times B {k}x{nb}",
+                           "nnz": nnz},
+                "roofline": {"bound": "hbm", "achieved": abytes / (t / 1e3) / 1e9, "peak": peak,
+                             "unit": "GB/s", "frac": abytes / (t / 1e3) / 1e9 / peak,
+                             "kernel": "k_block_csr", "traffic": None,
+                             "peak_kind": f"{peak_kind} hbm_gbs",
+                             "note": "B (4 MiB) is re-read from L2 per nonzero; HBM bytes count it once"},
+                "gpu_launches": 1,
+            })
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,13 +600,21 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the per-representation comparisons")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="built-in representation rules")
+    ap.add_argument("--no-clocks", action="store_true", help="skip the clock-sampling load phase")
+    ap.add_argument("--pairs", type=int, default=COUNT, help="batch size (smaller for profiling)")
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "dot", "matvec", "block", "csr"])
+    ap.add_argument("--block-m", type=int, default=16384, help="block workload rows (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "batched":
         run_gpu(args)
+    else:
+        run_secondary(args)
 
 
 if __name__ == "__main__":

@@ -73,7 +73,10 @@ typedef enum gfp_repr {
                                32-bit wrap count, and one correction by 2^64 mod p at the end */
     GFP_REPR_FP64 = 4,      /* 53-bit exact double accumulator reduced every k terms with the
                                floating-point reduction of Section 2.3 (p <= 94906266 only) */
-    GFP_REPR_COUNT_ = 5
+    GFP_REPR_F16TC = 5,     /* block product only: centred residues (Section 3.2.2) split into
+                               two balanced 8-bit digits, exact fp16 tensor-core products with
+                               fp32 accumulation over chunks of 1024 terms (p <= 65791) */
+    GFP_REPR_COUNT_ = 6
 } gfp_repr;
 
 typedef struct gfp_ctx gfp_ctx;
@@ -223,6 +226,40 @@ GFP_API gfp_status gfp_matvec(gfp_ctx *ctx, uint32_t p, uint64_t rows, uint64_t 
 GFP_API gfp_status gfp_matvec_iterate(gfp_ctx *ctx, uint32_t p, uint64_t n, const uint32_t *A,
                                       uint64_t lda, const uint32_t *x0, uint32_t *Y,
                                       uint32_t iters, void *stream);
+
+/* ---- block products (dense contraction of many dot products) ---- */
+
+/* C[i*ldc + j] = (sum_t A[i*lda + t] * B[t*ldb + j]) mod p, 0 <= i < m,
+ * 0 <= j < nb.  A (m x k), B (k x nb), C (m x nb): device, row-major,
+ * lda >= k, ldb >= nb, ldc >= nb; C must not overlap A or B.
+ * Path: with GFP_REPR_AUTO or GFP_REPR_F16TC and p <= 65791, A 16-byte
+ * aligned and lda a multiple of 4, the tensor-core kernel (two launches: B
+ * digit split, then the persistent product); otherwise the CUDA-core kernel
+ * with the representation the context resolves for (p, k) (forcing F16TC
+ * where it is not eligible gives GFP_ERR_UNSUPPORTED).  The tensor-core path
+ * uses the context's workspace (grown on demand, so call once outside stream
+ * capture for the largest shape) and must not run concurrently with another
+ * block product of the same context.  k == 0 writes zeros. */
+GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64_t k, uint64_t nb,
+                                    const uint32_t *A, uint64_t lda, const uint32_t *B,
+                                    uint64_t ldb, uint32_t *C, uint64_t ldc, void *stream);
+
+/* Sparse-row block product: A is m x k in CSR form (row_ptr[m+1] offsets
+ * into col[] and val[], column indices < k, values canonical residues), B is
+ * k x nb dense.  C[i*ldc + j] = (sum_q val[q] * B[col[q]*ldb + j]) mod p for
+ * row_ptr[i] <= q < row_ptr[i+1].  All arrays on the device; row_ptr must be
+ * non-decreasing with row_ptr[0] = 0 (checked on the device only when
+ * validation is enabled, together with col < k and the residues).  One launch. */
+GFP_API gfp_status gfp_matmul_block_csr(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64_t k,
+                                        uint64_t nb, const uint32_t *row_ptr, const uint32_t *col,
+                                        const uint32_t *val, const uint32_t *B, uint64_t ldb,
+                                        uint32_t *C, uint64_t ldc, void *stream);
+
+/* Synchronise the context's device and report whether a kernel of the
+ * context gave up on a bounded wait since the last check (GFP_ERR_TIMEOUT,
+ * after which the workspace is cleared so later calls start clean), or a
+ * CUDA error is pending (GFP_ERR_CUDA).  GFP_OK otherwise. */
+GFP_API gfp_status gfp_context_check(gfp_ctx *ctx);
 
 /* ---- install-time tuning (automated empirical optimisation, Section 4) ---- */
 

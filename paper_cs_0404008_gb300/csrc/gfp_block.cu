@@ -1,0 +1,654 @@
+// Block product over GF(p): C = A B mod p, A m x k, B k x nb (row-major
+// uint32 residues), the dense contraction at the heart of block methods.
+//
+// Tensor-core path (p <= 65791, the centred residues of Section 3.2.2 then
+// fit two balanced 8-bit digits):
+//   a in [0, p) is centred to s in [-(p-1)/2, (p-1)/2] and split exactly as
+//   s = 256 h + l with l in [-128, 127], h in [-128, 128].  Every digit is an
+//   exact fp16 value and every digit product is an integer of magnitude at
+//   most 2^14, so 1024 of them sum to at most 2^24: exact in an fp32
+//   accumulator.  A and B digits therefore go through tcgen05.mma kind::f16
+//   with fp32 accumulation in TMEM, and every 1024 terms (the exact chunk,
+//   Eq. (1) read with m = 24 for the fp32 significand) the four digit-product
+//   accumulators are recombined as hh*2^16 + (hl + lh)*2^8 + ll in int64,
+//   reduced mod p, and summed as residues.  Nothing is approximated.
+//   Roles per CTA (one CTA per SM, persistent over (tile, chunk) units):
+//     warp 0      bulk-copies the pre-split B digit tiles (TMA engine)
+//     warp 1      owns TMEM and issues the MMAs (one thread)
+//     warps 2-9   load A uint32 tiles from HBM, centre and split them into
+//                 the two fp16 digit tiles in 128-byte-swizzled shared memory
+//     warps 10-13 drain the accumulators (tcgen05.ld), recombine, reduce
+//   B's digits are stacked [hi | lo] along N (N = 128 per MMA), so one MMA
+//   per A digit yields both products with that digit.
+//   Units of one output tile may be split over two CTAs; their residue sums
+//   meet in a u32 workspace through atomics and the CTA that completes a
+//   tile (ticket counter) reduces it into C and clears the workspace.
+//
+// CUDA-core path (any p <= 2^32-1): shared-memory tiled product with the
+// per-thread unreduced accumulators of the dot-product kernels.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "gfp_internal.h"
+#include "gfp_tc.cuh"
+
+namespace gfp {
+namespace blk {
+
+constexpr int BM = 128;            // rows per tile (MMA M)
+constexpr int BK = 64;             // K per k-block: one 128-byte swizzle row of fp16
+constexpr int NT = 64;             // output columns per n-tile
+constexpr int MMA_N = 2 * NT;      // hi and lo digits of B stacked along N
+constexpr int KC = 16;             // k-blocks per exact chunk (1024 terms)
+constexpr int STAGES = 4;
+constexpr int A_DIGIT_BYTES = BM * BK * 2;                    // 16 KiB
+constexpr int B_TILE_BYTES = MMA_N * BK * 2;                  // 16 KiB
+constexpr int STAGE_BYTES = 2 * A_DIGIT_BYTES + B_TILE_BYTES; // 48 KiB
+constexpr int CONV_WARPS = 8;
+constexpr int EPI_WARPS = 4;
+constexpr int THREADS = 32 * (2 + CONV_WARPS + EPI_WARPS);   // 448
+constexpr uint32_t TMEM_COLS = 512;   // 2 accumulator sets x 2 digits x 128 columns
+constexpr uint64_t WAIT_NS = 2000000000ull;   // bounded waits: 2 s
+constexpr uint32_t IDESC = ptx::idesc_f16_f32(BM, MMA_N);
+
+struct Bars {
+    uint64_t full_b[STAGES];   // B digit tile landed (1 arrival + tx bytes)
+    uint64_t full_a[STAGES];   // A digit tiles written (one arrival per converter warp)
+    uint64_t empty[STAGES];    // MMAs reading the stage completed (tcgen05.commit)
+    uint64_t acc_full[2];      // accumulator set ready (tcgen05.commit)
+    uint64_t acc_empty[2];     // accumulator set drained (one arrival per epilogue warp)
+    uint64_t drain;            // all MMAs issued by this CTA completed
+    uint32_t tmem_base;
+    uint32_t abort;
+    uint32_t last_flag;
+};
+constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + (size_t)STAGES * STAGE_BYTES + 1024;
+
+struct Args {
+    const uint32_t *A;
+    uint64_t lda, m, k, nb;
+    const uint8_t *Bimg;      // [n_tiles][kblocks] tiles of B_TILE_BYTES
+    uint32_t *C;
+    uint64_t ldc;
+    uint32_t *Cacc;           // m x (n_tiles*NT) u32 partial residue sums (zero outside calls)
+    uint32_t *tickets;        // n_tiles*m_tiles chunk counters (zero outside calls)
+    uint32_t *err;            // bit 0: a bounded wait expired
+    Mod mod;
+    uint64_t off;             // multiple of p >= 2^41 making recombined values non-negative
+    uint32_t half;            // (p-1)/2
+    uint32_t m_tiles, n_tiles, kblocks, chunks;
+    uint64_t units;
+};
+
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile uint32_t *abort,
+                                         uint32_t *err)
+{
+    uint64_t t0 = 0;
+    for (uint32_t i = 0;; ++i) {
+        if (ptx::mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u) {
+            if (*abort) return false;
+            const uint64_t t = ptx::globaltimer();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > WAIT_NS) {
+                *abort = 1u;
+                atomicOr(err, 1u);
+                return false;
+            }
+        }
+    }
+}
+
+struct UnitPos {
+    uint32_t nt, mt, c, kb0, kb1;
+};
+
+__device__ __forceinline__ UnitPos unit_pos(const Args &a, uint64_t u)
+{
+    UnitPos q;
+    q.c = (uint32_t)(u % a.chunks);
+    const uint64_t tile = u / a.chunks;
+    q.mt = (uint32_t)(tile % a.m_tiles);
+    q.nt = (uint32_t)(tile / a.m_tiles);
+    q.kb0 = q.c * KC;
+    q.kb1 = min(q.kb0 + (uint32_t)KC, a.kblocks);
+    return q;
+}
+
+// Centre a residue and split it into two balanced 8-bit digits (fp16 pair).
+__device__ __forceinline__ void split_digits(uint32_t a, uint32_t p, uint32_t half, __half &h,
+                                             __half &l)
+{
+    const int s = (a > half) ? (int)a - (int)p : (int)a;
+    const int lo = ((s + 128) & 255) - 128;
+    const int hi = (s - lo) >> 8;
+    h = __int2half_rn(hi);
+    l = __int2half_rn(lo);
+}
+
+__device__ __forceinline__ uint32_t pack2(__half a, __half b)
+{
+    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+// A tile loader of one converter thread: 8 chunks of 4 consecutive K of one row.
+struct ATileRegs {
+    uint4 v[8];
+};
+
+__device__ __forceinline__ void load_a_tile(const Args &a, uint32_t mt, uint32_t kb, int ct,
+                                            ATileRegs &r)
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int q = ct + 256 * i;
+        const int row = q >> 4, c4 = q & 15;
+        const uint64_t gr = (uint64_t)mt * BM + row;
+        const uint64_t gc = (uint64_t)kb * BK + (uint64_t)c4 * 4;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gr < a.m) {
+            const uint32_t *src = a.A + gr * a.lda + gc;
+            if (gc + 3 < a.k) {
+                v = __ldcs(reinterpret_cast<const uint4 *>(src));
+            } else {
+                if (gc + 0 < a.k) v.x = __ldcs(src + 0);
+                if (gc + 1 < a.k) v.y = __ldcs(src + 1);
+                if (gc + 2 < a.k) v.z = __ldcs(src + 2);
+            }
+        }
+        r.v[i] = v;
+    }
+}
+
+__device__ __forceinline__ void store_a_digits(const Args &a, uint8_t *stage, int ct,
+                                               const ATileRegs &r)
+{
+    uint8_t *th = stage;                    // high digits
+    uint8_t *tl = stage + A_DIGIT_BYTES;    // low digits
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int q = ct + 256 * i;
+        const int row = q >> 4, c4 = q & 15;
+        __half h0, h1, h2, h3, l0, l1, l2, l3;
+        split_digits(r.v[i].x, a.mod.p, a.half, h0, l0);
+        split_digits(r.v[i].y, a.mod.p, a.half, h1, l1);
+        split_digits(r.v[i].z, a.mod.p, a.half, h2, l2);
+        split_digits(r.v[i].w, a.mod.p, a.half, h3, l3);
+        // 128-byte swizzle: 16-byte chunk j of row r sits at chunk j ^ (r & 7)
+        const int j = c4 >> 1, halfsel = c4 & 1;
+        const uint32_t off = (uint32_t)row * 128u + ((uint32_t)(j ^ (row & 7)) << 4) + (halfsel << 3);
+        *reinterpret_cast<uint2 *>(th + off) = make_uint2(pack2(h0, h1), pack2(h2, h3));
+        *reinterpret_cast<uint2 *>(tl + off) = make_uint2(pack2(l0, l1), pack2(l2, l3));
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 1) k_block_tc(Args a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    Bars *bars = reinterpret_cast<Bars *>(smem + (size_t)STAGES * STAGE_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const uint64_t u0 = a.units * blockIdx.x / gridDim.x;
+    const uint64_t u1 = a.units * (blockIdx.x + 1) / gridDim.x;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            ptx::mbar_init(ptx::smem_u32(&bars->full_b[s]), 1);
+            ptx::mbar_init(ptx::smem_u32(&bars->full_a[s]), CONV_WARPS);
+            ptx::mbar_init(ptx::smem_u32(&bars->empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(ptx::smem_u32(&bars->acc_full[b]), 1);
+            ptx::mbar_init(ptx::smem_u32(&bars->acc_empty[b]), EPI_WARPS);
+        }
+        ptx::mbar_init(ptx::smem_u32(&bars->drain), 1);
+        bars->abort = 0;
+        bars->last_flag = 0;
+        ptx::fence_barrier_init();
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(ptx::smem_u32(&bars->tmem_base), TMEM_COLS);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = bars->tmem_base;
+    volatile uint32_t *abort = &bars->abort;
+
+    if (warp == 0) {
+        // ---------------- B digit tiles: bulk copies ----------------
+        if (lane == 0) {
+            uint32_t it = 0;
+            int armed[STAGES];
+            for (int s = 0; s < STAGES; ++s) armed[s] = -1;
+            bool ok = true;
+            for (uint64_t u = u0; u < u1 && ok; ++u) {
+                const UnitPos q = unit_pos(a, u);
+                for (uint32_t kb = q.kb0; kb < q.kb1 && ok; ++kb, ++it) {
+                    const uint32_t s = it % STAGES, round = it / STAGES;
+                    if (round > 0 &&
+                        !wait_bar(ptx::smem_u32(&bars->empty[s]), (round - 1) & 1, abort, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = ptx::smem_u32(&bars->full_b[s]);
+                    ptx::mbar_arrive_expect_tx(fb, B_TILE_BYTES);
+                    ptx::bulk_g2s(ptx::smem_u32(smem + (size_t)s * STAGE_BYTES + 2 * A_DIGIT_BYTES),
+                                  a.Bimg + ((uint64_t)q.nt * a.kblocks + kb) * B_TILE_BYTES,
+                                  B_TILE_BYTES, fb);
+                    armed[s] = (int)round;
+                }
+            }
+            if (!ok) {
+                // let copies already issued land before the CTA can exit
+                for (int s = 0; s < STAGES; ++s) {
+                    if (armed[s] < 0) continue;
+                    const uint64_t t0 = ptx::globaltimer();
+                    while (!ptx::mbar_try_wait(ptx::smem_u32(&bars->full_b[s]), armed[s] & 1) &&
+                           ptx::globaltimer() - t0 < WAIT_NS) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issue (one thread) ----------------
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            uint64_t idx = 0;
+            for (uint64_t u = u0; u < u1 && ok; ++u, ++idx) {
+                const UnitPos q = unit_pos(a, u);
+                const uint32_t b = (uint32_t)(idx & 1), use = (uint32_t)(idx >> 1);
+                if (use > 0 &&
+                    !wait_bar(ptx::smem_u32(&bars->acc_empty[b]), (use - 1) & 1, abort, a.err)) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint32_t d_hi = tmem + b * 256u;         // A high digit x [B hi | B lo]
+                const uint32_t d_lo = tmem + b * 256u + 128u;  // A low digit  x [B hi | B lo]
+                for (uint32_t kb = q.kb0; kb < q.kb1; ++kb, ++it) {
+                    const uint32_t s = it % STAGES, round = it / STAGES;
+                    if (!wait_bar(ptx::smem_u32(&bars->full_b[s]), round & 1, abort, a.err) ||
+                        !wait_bar(ptx::smem_u32(&bars->full_a[s]), round & 1, abort, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint32_t base = ptx::smem_u32(smem + (size_t)s * STAGE_BYTES);
+                    const uint64_t dah = ptx::sdesc_k_sw128(base);
+                    const uint64_t dal = ptx::sdesc_k_sw128(base + A_DIGIT_BYTES);
+                    const uint64_t db = ptx::sdesc_k_sw128(base + 2 * A_DIGIT_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint32_t acc = (kb > q.kb0 || kk > 0) ? 1u : 0u;
+                        // advance 16 fp16 (32 bytes) along K inside the swizzle atom
+                        ptx::mma_f16(d_hi, dah + 2 * kk, db + 2 * kk, IDESC, acc);
+                        ptx::mma_f16(d_lo, dal + 2 * kk, db + 2 * kk, IDESC, acc);
+                    }
+                    ptx::mma_commit(ptx::smem_u32(&bars->empty[s]));
+                }
+                if (!ok) break;
+                ptx::mma_commit(ptx::smem_u32(&bars->acc_full[b]));
+            }
+            // every MMA issued by this CTA has completed before TMEM is freed
+            ptx::mma_commit(ptx::smem_u32(&bars->drain));
+            const uint64_t t0 = ptx::globaltimer();
+            while (!ptx::mbar_try_wait(ptx::smem_u32(&bars->drain), 0) &&
+                   ptx::globaltimer() - t0 < WAIT_NS) {
+            }
+        }
+    } else if (warp < 2 + CONV_WARPS) {
+        // ---------------- A: HBM -> centred fp16 digits in shared memory ----------------
+        const int ct = threadIdx.x - 64;   // 0..255
+        const int cw = warp - 2;
+        uint32_t it = 0;
+        // (unit, k-block) sequence with one tile of register prefetch
+        uint64_t u = u0;
+        UnitPos q;
+        uint32_t kb = 0;
+        if (u < u1) {
+            q = unit_pos(a, u);
+            kb = q.kb0;
+        }
+        ATileRegs cur, nxt;
+        if (u < u1) load_a_tile(a, q.mt, kb, ct, cur);
+        while (u < u1) {
+            // position of the next tile
+            uint64_t nu = u;
+            UnitPos nq = q;
+            uint32_t nkb = kb + 1;
+            if (nkb >= q.kb1) {
+                ++nu;
+                if (nu < u1) {
+                    nq = unit_pos(a, nu);
+                    nkb = nq.kb0;
+                }
+            }
+            if (nu < u1) load_a_tile(a, nq.mt, nkb, ct, nxt);
+            const uint32_t s = it % STAGES, round = it / STAGES;
+            bool ok = true;
+            if (round > 0) {
+                if (lane == 0)
+                    ok = wait_bar(ptx::smem_u32(&bars->empty[s]), (round - 1) & 1, abort, a.err);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            }
+            if (!ok) break;
+            store_a_digits(a, smem + (size_t)s * STAGE_BYTES, ct, cur);
+            ptx::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&bars->full_a[s]));
+            (void)cw;
+            ++it;
+            u = nu;
+            q = nq;
+            kb = nkb;
+            cur = nxt;
+        }
+    } else {
+        // ---------------- epilogue: TMEM -> residues ----------------
+        const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31
+        const int row_in_tile = quarter * 32 + lane;
+        const uint32_t lane_bits = (uint32_t)(quarter * 32) << 16;
+        uint32_t res[NT];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) res[j] = 0;
+        uint32_t seg_chunks = 0;
+        uint64_t idx = 0;
+        bool ok = true;
+        for (uint64_t u = u0; u < u1 && ok; ++u, ++idx) {
+            const UnitPos q = unit_pos(a, u);
+            const uint32_t b = (uint32_t)(idx & 1), use = (uint32_t)(idx >> 1);
+            bool got = true;
+            if (lane == 0) got = wait_bar(ptx::smem_u32(&bars->acc_full[b]), use & 1, abort, a.err);
+            got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+            // decide together: the epilogue warps meet at named barriers below
+            if (ptx::bar_red_or<1, EPI_WARPS * 32>(!got || *abort != 0)) {
+                ok = false;
+                break;
+            }
+            ptx::tc_fence_after();
+            const uint32_t d_hi = tmem + lane_bits + b * 256u;
+            const uint32_t d_lo = d_hi + 128u;
+#pragma unroll
+            for (int g = 0; g < NT / 8; ++g) {
+                uint32_t hh[8], hl[8], lh[8], ll[8];
+                ptx::tmem_ld8(d_hi + g * 8, hh);
+                ptx::tmem_ld8(d_hi + NT + g * 8, hl);
+                ptx::tmem_ld8(d_lo + g * 8, lh);
+                ptx::tmem_ld8(d_lo + NT + g * 8, ll);
+                ptx::tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const long long vhh = __float2int_rn(__uint_as_float(hh[j]));
+                    const long long vx = (long long)__float2int_rn(__uint_as_float(hl[j])) +
+                                         (long long)__float2int_rn(__uint_as_float(lh[j]));
+                    const long long vll = __float2int_rn(__uint_as_float(ll[j]));
+                    const long long v = vhh * 65536ll + vx * 256ll + vll;
+                    res[g * 8 + j] += reduce64((uint64_t)(v + (long long)a.off), a.mod);
+                }
+            }
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&bars->acc_empty[b]));
+            ++seg_chunks;
+            // end of this CTA's run of units on the output tile?
+            bool flush = (u + 1 == u1);
+            if (!flush) {
+                const UnitPos nq = unit_pos(a, u + 1);
+                flush = (nq.mt != q.mt) || (nq.nt != q.nt);
+            }
+            if (flush) {
+                const uint64_t grow = (uint64_t)q.mt * BM + row_in_tile;
+                const uint64_t ldacc = (uint64_t)a.n_tiles * NT;
+                const uint64_t col0 = (uint64_t)q.nt * NT;
+                if (grow < a.m) {
+#pragma unroll
+                    for (int j = 0; j < NT; ++j)
+                        if (col0 + j < a.nb) atomicAdd(&a.Cacc[grow * ldacc + col0 + j], res[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < NT; ++j) res[j] = 0;
+                __threadfence();
+                asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32));
+                if (warp == 2 + CONV_WARPS && lane == 0) {
+                    const uint32_t t = a.n_tiles > 0 ? q.nt * a.m_tiles + q.mt : 0;
+                    const uint32_t old = atomicAdd(&a.tickets[t], seg_chunks);
+                    bars->last_flag = (old + seg_chunks == a.chunks) ? 1u : 0u;
+                    __threadfence();
+                }
+                asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32));
+                if (bars->last_flag) {
+                    if (grow < a.m) {
+                        for (int j = 0; j < NT; ++j) {
+                            if (col0 + j >= a.nb) break;
+                            uint32_t *cell = &a.Cacc[grow * ldacc + col0 + j];
+                            const uint32_t v = atomicExch(cell, 0u);
+                            a.C[grow * a.ldc + col0 + j] = reduce64(v, a.mod);
+                        }
+                    }
+                    asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32));
+                    if (warp == 2 + CONV_WARPS && lane == 0) {
+                        atomicExch(&a.tickets[q.nt * a.m_tiles + q.mt], 0u);
+                        bars->last_flag = 0;
+                    }
+                }
+                asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32));
+                seg_chunks = 0;
+            }
+        }
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// B (k x nb, row-major) -> per (n-tile, k-block) tiles of 128 rows x 64 K
+// fp16 digits in the 128-byte swizzled K-major layout: rows 0..63 hold the
+// high digits of output columns nt*64 + r, rows 64..127 the low digits.
+__global__ void k_block_prep_b(const uint32_t *B, uint64_t ldb, uint64_t k, uint64_t nb, Mod mod,
+                               uint32_t half, uint32_t kblocks, uint8_t *img)
+{
+    const uint32_t tile = blockIdx.x;            // nt * kblocks + kb
+    const uint32_t nt = tile / kblocks, kb = tile % kblocks;
+    uint8_t *out = img + (uint64_t)tile * B_TILE_BYTES;
+    for (int t = threadIdx.x; t < 64 * 8; t += blockDim.x) {
+        const int col = t >> 3, j = t & 7;       // output column within the tile, 16-byte chunk
+        const uint64_t gcol = (uint64_t)nt * NT + col;
+        __half hi[8], lo[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const uint64_t gk = (uint64_t)kb * BK + j * 8 + e;
+            uint32_t v = 0;
+            if (gk < k && gcol < nb) v = B[gk * ldb + gcol];
+            split_digits(v, mod.p, half, hi[e], lo[e]);
+        }
+        uint4 wh, wl;
+        wh.x = pack2(hi[0], hi[1]); wh.y = pack2(hi[2], hi[3]);
+        wh.z = pack2(hi[4], hi[5]); wh.w = pack2(hi[6], hi[7]);
+        wl.x = pack2(lo[0], lo[1]); wl.y = pack2(lo[2], lo[3]);
+        wl.z = pack2(lo[4], lo[5]); wl.w = pack2(lo[6], lo[7]);
+        const int rh = col, rl = col + 64;
+        *reinterpret_cast<uint4 *>(out + rh * 128 + ((j ^ (rh & 7)) << 4)) = wh;
+        *reinterpret_cast<uint4 *>(out + rl * 128 + ((j ^ (rl & 7)) << 4)) = wl;
+    }
+}
+
+// ---------------- CUDA-core path ----------------
+constexpr int CC_TM = 64, CC_TN = 64, CC_TK = 32, CC_THREADS = 256;
+
+template <class Acc>
+__global__ void __launch_bounds__(CC_THREADS)
+    k_block_cc(Mod mod, uint64_t kk_bound, uint64_t m, uint64_t k, uint64_t nb,
+               const uint32_t *__restrict__ A, uint64_t lda, const uint32_t *__restrict__ B,
+               uint64_t ldb, uint32_t *__restrict__ C, uint64_t ldc)
+{
+    __shared__ __align__(16) uint32_t As[CC_TK][CC_TM];   // transposed: [k][row]
+    __shared__ __align__(16) uint32_t Bs[CC_TK][CC_TN];
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const uint64_t row0 = (uint64_t)blockIdx.y * CC_TM, col0 = (uint64_t)blockIdx.x * CC_TN;
+    Acc acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j].init(mod, kk_bound);
+    for (uint64_t k0 = 0; k0 < k; k0 += CC_TK) {
+        // A tile: 64 rows x 32 K; thread -> row t/4, 8 consecutive K
+        {
+            const int r = t >> 2, kc = (t & 3) * 8;
+            const uint64_t gr = row0 + r;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint64_t gk = k0 + kc + e;
+                As[kc + e][r] = (gr < m && gk < k) ? __ldg(A + gr * lda + gk) : 0u;
+            }
+        }
+        // B tile: 32 K x 64 columns; thread -> K t/8, 8 consecutive columns
+        {
+            const int r = t >> 3, cc = (t & 7) * 8;
+            const uint64_t gk = k0 + r;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint64_t gc = col0 + cc + e;
+                Bs[r][cc + e] = (gk < k && gc < nb) ? __ldg(B + gk * ldb + gc) : 0u;
+            }
+        }
+        __syncthreads();
+        const int kmax = (int)min((uint64_t)CC_TK, k - k0);
+        for (int kk = 0; kk < kmax; ++kk) {
+            const uint4 av = *reinterpret_cast<const uint4 *>(&As[kk][ty * 4]);
+            const uint4 bv = *reinterpret_cast<const uint4 *>(&Bs[kk][tx * 4]);
+            const uint32_t ar[4] = {av.x, av.y, av.z, av.w};
+            const uint32_t br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j].add(ar[i], br[j], mod);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint64_t gr = row0 + ty * 4 + i;
+        if (gr >= m) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint64_t gc = col0 + tx * 4 + j;
+            if (gc < nb) C[gr * ldc + gc] = acc[i][j].residue(mod);
+        }
+    }
+}
+
+}  // namespace blk
+
+// ---------------- launchers ----------------
+
+bool block_tc_eligible(uint32_t p, const uint32_t *A, uint64_t lda)
+{
+    return p >= 2 && p <= BLOCK_TC_MAX_P && ((((uintptr_t)A) & 15u) == 0) && (lda % 4 == 0);
+}
+
+size_t block_tc_bimg_bytes(uint64_t k, uint64_t nb)
+{
+    const uint64_t kblocks = (k + blk::BK - 1) / blk::BK;
+    const uint64_t n_tiles = (nb + blk::NT - 1) / blk::NT;
+    return (n_tiles * kblocks * (uint64_t)blk::B_TILE_BYTES + 255) & ~(size_t)255;
+}
+
+size_t block_tc_workspace_bytes(uint64_t m, uint64_t k, uint64_t nb)
+{
+    const uint64_t kblocks = (k + blk::BK - 1) / blk::BK;
+    const uint64_t n_tiles = (nb + blk::NT - 1) / blk::NT;
+    const uint64_t m_tiles = (m + blk::BM - 1) / blk::BM;
+    size_t b = n_tiles * kblocks * (uint64_t)blk::B_TILE_BYTES;
+    b = (b + 255) & ~(size_t)255;
+    b += ((m * n_tiles * blk::NT * 4 + 255) & ~(size_t)255);
+    b += ((n_tiles * m_tiles * 4 + 255) & ~(size_t)255);
+    b += 256;   // error flag
+    return b;
+}
+
+uint32_t *block_tc_err_flag(void *ws, uint64_t m, uint64_t k, uint64_t nb)
+{
+    return (uint32_t *)((uint8_t *)ws + block_tc_workspace_bytes(m, k, nb) - 256);
+}
+
+cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb, const uint32_t *A,
+                            uint64_t lda, const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc,
+                            void *ws, int sm_count, cudaStream_t s, int *launches)
+{
+    using namespace blk;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    Args a;
+    a.A = A;
+    a.lda = lda;
+    a.m = m;
+    a.k = k;
+    a.nb = nb;
+    a.C = C;
+    a.ldc = ldc;
+    a.mod = mod;
+    a.half = (mod.p - 1) / 2;
+    a.kblocks = (uint32_t)((k + BK - 1) / BK);
+    a.n_tiles = (uint32_t)((nb + NT - 1) / NT);
+    a.m_tiles = (uint32_t)((m + BM - 1) / BM);
+    a.chunks = (a.kblocks + KC - 1) / KC;
+    a.units = (uint64_t)a.n_tiles * a.m_tiles * a.chunks;
+    const uint64_t two41 = 1ull << 41;
+    a.off = (two41 / mod.p + 1) * (uint64_t)mod.p;
+    uint8_t *w = (uint8_t *)ws;
+    size_t o = (size_t)a.n_tiles * a.kblocks * B_TILE_BYTES;
+    o = (o + 255) & ~(size_t)255;
+    a.Bimg = w;
+    a.Cacc = (uint32_t *)(w + o);
+    o += ((m * a.n_tiles * NT * 4 + 255) & ~(size_t)255);
+    a.tickets = (uint32_t *)(w + o);
+    o += ((a.n_tiles * a.m_tiles * 4 + 255) & ~(size_t)255);
+    a.err = (uint32_t *)(w + o);
+    k_block_prep_b<<<a.n_tiles * a.kblocks, 256, 0, s>>>(B, ldb, k, nb, mod, a.half, a.kblocks,
+                                                         (uint8_t *)a.Bimg);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const uint64_t grid = std::min<uint64_t>(a.units, (uint64_t)sm_count);
+    k_block_tc<<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(a);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+template <class Acc>
+static cudaError_t cc_launch(const Mod &mod, uint64_t kb, uint64_t m, uint64_t k, uint64_t nb,
+                             const uint32_t *A, uint64_t lda, const uint32_t *B, uint64_t ldb,
+                             uint32_t *C, uint64_t ldc, cudaStream_t s)
+{
+    using namespace blk;
+    dim3 grid((unsigned)((nb + CC_TN - 1) / CC_TN), (unsigned)((m + CC_TM - 1) / CC_TM));
+    k_block_cc<Acc><<<grid, CC_THREADS, 0, s>>>(mod, kb, m, k, nb, A, lda, B, ldb, C, ldc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_cc(Repr r, const Mod &mod, uint64_t kbound, uint64_t m, uint64_t k,
+                            uint64_t nb, const uint32_t *A, uint64_t lda, const uint32_t *B,
+                            uint64_t ldb, uint32_t *C, uint64_t ldc, cudaStream_t s)
+{
+    switch (r) {
+    case U64_BLOCK: return cc_launch<AccBlock>(mod, kbound, m, k, nb, A, lda, B, ldb, C, ldc, s);
+    case U64_CARRY: return cc_launch<AccCarry>(mod, kbound, m, k, nb, A, lda, B, ldb, C, ldc, s);
+    case FP64: return cc_launch<AccF64>(mod, kbound, m, k, nb, A, lda, B, ldb, C, ldc, s);
+    default: return cc_launch<AccPerTerm>(mod, kbound, m, k, nb, A, lda, B, ldb, C, ldc, s);
+    }
+}
+
+}  // namespace gfp

@@ -71,6 +71,26 @@ cudaError_t launch_matvec(Repr r, const Mod &m, uint64_t k, uint64_t rows, uint6
                           const uint32_t *A, uint64_t lda, const uint32_t *x, uint32_t *y,
                           int sm_count, cudaStream_t s);
 
+// Block product (gfp_block.cu).  The tensor-core path needs the centred
+// residues to fit two balanced 8-bit digits: (p-1)/2 <= 32895.
+constexpr uint32_t BLOCK_TC_MAX_P = 65791;
+bool block_tc_eligible(uint32_t p, const uint32_t *A, uint64_t lda);
+size_t block_tc_workspace_bytes(uint64_t m, uint64_t k, uint64_t nb);
+size_t block_tc_bimg_bytes(uint64_t k, uint64_t nb);   // the rest must be zero at launch
+cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb, const uint32_t *A,
+                            uint64_t lda, const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc,
+                            void *ws, int sm_count, cudaStream_t s, int *launches);
+uint32_t *block_tc_err_flag(void *ws, uint64_t m, uint64_t k, uint64_t nb);
+cudaError_t launch_block_cc(Repr r, const Mod &mod, uint64_t kbound, uint64_t m, uint64_t k,
+                            uint64_t nb, const uint32_t *A, uint64_t lda, const uint32_t *B,
+                            uint64_t ldb, uint32_t *C, uint64_t ldc, cudaStream_t s);
+// Sparse-row block product (gfp_csr.cu).
+cudaError_t launch_block_csr(Repr r, const Mod &mod, uint64_t kbound, uint64_t m, uint64_t k,
+                             uint64_t nb,
+                             const uint32_t *row_ptr, const uint32_t *col, const uint32_t *val,
+                             const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc,
+                             int sm_count, cudaStream_t s);
+
 }  // namespace gfp
 
 // Tuned plan entry: representation and unit chunk per (p, length bucket).
@@ -107,6 +127,12 @@ struct gfp_ctx {
     size_t stage_elems = 0;
     uint32_t *stage_out = nullptr;
     size_t stage_out_elems = 0;
+
+    // block-product workspace (B digit image, partial sums, tickets, error
+    // flag); zero outside calls except the B image; grown on demand
+    void *blk_ws = nullptr;
+    size_t blk_ws_bytes = 0;
+    uint64_t blk_m = 0, blk_k = 0, blk_nb = 0;   // shape whose error flag is live
 
     // tuned plan: (p, lg_n) -> entry
     std::map<std::pair<uint32_t, uint32_t>, gfp_plan_entry> plan;

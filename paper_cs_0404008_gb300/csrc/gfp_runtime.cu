@@ -391,6 +391,7 @@ GFP_API gfp_status gfp_context_destroy(gfp_ctx *ctx)
     if (ctx->bw) cudaFree(ctx->bw);
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->stage_out) cudaFree(ctx->stage_out);
+    if (ctx->blk_ws) cudaFree(ctx->blk_ws);
     delete ctx;
     return GFP_OK;
 }
@@ -654,6 +655,131 @@ GFP_API gfp_status gfp_matvec_iterate(gfp_ctx *ctx, uint32_t p, uint64_t n, cons
     }
     GFP_CUDA_TRY(cudaGraphLaunch(it->second, s));
     ctx->launches += iters;
+    return GFP_OK;
+}
+
+static gfp_status check_range_rows(gfp_ctx *ctx, const uint32_t *M, uint64_t rows, uint64_t cols,
+                                   uint64_t ld, uint32_t p, cudaStream_t s)
+{
+    if (!ctx->validate) return GFP_OK;
+    if (ld == cols) return check_range(ctx, M, rows * cols, p, s);
+    for (uint64_t i = 0; i < rows; ++i) {
+        gfp_status st = check_range(ctx, M + i * ld, cols, p, s);
+        if (st != GFP_OK) return st;
+    }
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64_t k, uint64_t nb,
+                                    const uint32_t *A, uint64_t lda, const uint32_t *B,
+                                    uint64_t ldb, uint32_t *C, uint64_t ldc, void *stream)
+{
+    if (!ctx || p < 2 || lda < k || ldb < nb || ldc < nb) return GFP_ERR_INVALID;
+    if ((m && nb && !C) || (m && k && !A) || (k && nb && !B)) return GFP_ERR_INVALID;
+    if ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 3u) return GFP_ERR_INVALID;
+    if (m == 0 || nb == 0) return GFP_OK;
+    cudaStream_t s = as_stream(stream);
+    if (k == 0) {
+        GFP_CUDA_TRY(cudaMemset2DAsync(C, ldc * 4, 0, nb * 4, m, s));
+        return GFP_OK;
+    }
+    const bool tc_ok = block_tc_eligible(p, A, lda);
+    bool use_tc = false;
+    Repr r = U64_CARRY;
+    if (ctx->forced == GFP_REPR_F16TC) {
+        if (!tc_ok) return GFP_ERR_UNSUPPORTED;
+        use_tc = true;
+    } else if (ctx->forced == GFP_REPR_AUTO && tc_ok) {
+        use_tc = true;
+    } else if (!resolve_repr(ctx, GFP_REPR_AUTO, p, k, &r)) {
+        return GFP_ERR_UNSUPPORTED;
+    }
+    if (ctx->validate) {
+        gfp_status st = check_range_rows(ctx, A, m, k, lda, p, s);
+        if (st == GFP_OK) st = check_range_rows(ctx, B, k, nb, ldb, p, s);
+        if (st != GFP_OK) return st;
+    }
+    const Mod mod = make_mod(p);
+    if (!use_tc) {
+        GFP_CUDA_TRY(launch_block_cc(r, mod, k_for(r, p), m, k, nb, A, lda, B, ldb, C, ldc, s));
+        ctx->launches++;
+        return GFP_OK;
+    }
+    std::lock_guard<std::mutex> g(ctx->mu);
+    const size_t need = block_tc_workspace_bytes(m, k, nb);
+    if (need > ctx->blk_ws_bytes) {
+        GFP_CUDA_TRY(cudaDeviceSynchronize());
+        if (ctx->blk_ws) cudaFree(ctx->blk_ws);
+        ctx->blk_ws = nullptr;
+        ctx->blk_ws_bytes = 0;
+        if (cudaMalloc(&ctx->blk_ws, need) != cudaSuccess) return GFP_ERR_NOMEM;
+        GFP_CUDA_TRY(cudaMemset(ctx->blk_ws, 0, need));
+        ctx->blk_ws_bytes = need;
+    }
+    if (m != ctx->blk_m || k != ctx->blk_k || nb != ctx->blk_nb) {
+        // the partial-sum region moves with the shape: clear it
+        const size_t z = block_tc_bimg_bytes(k, nb);
+        GFP_CUDA_TRY(cudaMemsetAsync((uint8_t *)ctx->blk_ws + z, 0, need - z, s));
+        ctx->blk_m = m;
+        ctx->blk_k = k;
+        ctx->blk_nb = nb;
+    }
+    int launches = 0;
+    GFP_CUDA_TRY(launch_block_tc(mod, m, k, nb, A, lda, B, ldb, C, ldc, ctx->blk_ws, ctx->sm_count,
+                                 s, &launches));
+    ctx->launches += launches;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_matmul_block_csr(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64_t k,
+                                        uint64_t nb, const uint32_t *row_ptr, const uint32_t *col,
+                                        const uint32_t *val, const uint32_t *B, uint64_t ldb,
+                                        uint32_t *C, uint64_t ldc, void *stream)
+{
+    if (!ctx || p < 2 || ldb < nb || ldc < nb) return GFP_ERR_INVALID;
+    if (m && (!row_ptr || (nb && !C))) return GFP_ERR_INVALID;
+    if ((((uintptr_t)row_ptr) | ((uintptr_t)col) | ((uintptr_t)val) | ((uintptr_t)B) |
+         ((uintptr_t)C)) & 3u)
+        return GFP_ERR_INVALID;
+    if (m == 0 || nb == 0) return GFP_OK;
+    cudaStream_t s = as_stream(stream);
+    Repr r;
+    if (!resolve_repr(ctx, GFP_REPR_AUTO, p, k, &r)) return GFP_ERR_UNSUPPORTED;
+    if (ctx->validate) {
+        // structure: row_ptr read back on the host (validation mode synchronises anyway)
+        std::vector<uint32_t> rp(m + 1);
+        GFP_CUDA_TRY(cudaMemcpyAsync(rp.data(), row_ptr, (m + 1) * 4, cudaMemcpyDeviceToHost, s));
+        GFP_CUDA_TRY(cudaStreamSynchronize(s));
+        if (rp[0] != 0) return GFP_ERR_INVALID;
+        for (uint64_t i = 0; i < m; ++i)
+            if (rp[i + 1] < rp[i]) return GFP_ERR_INVALID;
+        const uint64_t nnz = rp[m];
+        if (nnz && (!col || !val)) return GFP_ERR_INVALID;
+        gfp_status st = check_range(ctx, col, nnz, k ? (uint32_t)std::min<uint64_t>(k, 0xFFFFFFFFull) : 0u, s);
+        if (st == GFP_ERR_RANGE) return GFP_ERR_INVALID;
+        if (st == GFP_OK) st = check_range(ctx, val, nnz, p, s);
+        if (st == GFP_OK) st = check_range_rows(ctx, B, k, nb, ldb, p, s);
+        if (st != GFP_OK) return st;
+    }
+    GFP_CUDA_TRY(launch_block_csr(r, make_mod(p), k_for(r, p), m, k, nb, row_ptr, col, val, B, ldb,
+                                  C, ldc, ctx->sm_count, s));
+    ctx->launches++;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_context_check(gfp_ctx *ctx)
+{
+    if (!ctx) return GFP_ERR_INVALID;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return GFP_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return GFP_ERR_CUDA;
+    if (!ctx->blk_ws) return GFP_OK;
+    uint32_t *flag = block_tc_err_flag(ctx->blk_ws, ctx->blk_m, ctx->blk_k, ctx->blk_nb);
+    uint32_t h = 0;
+    GFP_CUDA_TRY(cudaMemcpy(&h, flag, 4, cudaMemcpyDeviceToHost));
+    if (h) {
+        GFP_CUDA_TRY(cudaMemset(ctx->blk_ws, 0, ctx->blk_ws_bytes));
+        return GFP_ERR_TIMEOUT;
+    }
     return GFP_OK;
 }
 

@@ -31,7 +31,8 @@ GFP_REPR_PERTERM = 1
 GFP_REPR_U64_BLOCK = 2
 GFP_REPR_U64_CARRY = 3
 GFP_REPR_FP64 = 4
-REPR_NAMES = {0: "auto", 1: "perterm", 2: "u64_block", 3: "u64_carry", 4: "fp64"}
+GFP_REPR_F16TC = 5
+REPR_NAMES = {0: "auto", 1: "perterm", 2: "u64_block", 3: "u64_carry", 4: "fp64", 5: "f16tc"}
 
 _vp = ctypes.c_void_p
 _u32 = ctypes.c_uint32
@@ -76,6 +77,10 @@ _SIGS = {
     "gfp_dot_batched_host": (_int, [_vp, _u64, _vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp]),
     "gfp_matvec": (_int, [_vp, _u32, _u64, _u64, _vp, _u64, _vp, _vp, _vp]),
     "gfp_matvec_iterate": (_int, [_vp, _u32, _u64, _vp, _u64, _vp, _vp, _u32, _vp]),
+    "gfp_matmul_block": (_int, [_vp, _u32, _u64, _u64, _u64, _vp, _u64, _vp, _u64, _vp, _u64, _vp]),
+    "gfp_matmul_block_csr": (_int, [_vp, _u32, _u64, _u64, _u64, _vp, _vp, _vp, _vp, _u64, _vp, _u64,
+                                    _vp]),
+    "gfp_context_check": (_int, [_vp]),
     "gfp_tune": (_int, [_vp, _vp, _u32, _u32, _u32, ctypes.c_char_p]),
     "gfp_plan_load": (_int, [_vp, ctypes.c_char_p]),
     "gfp_plan_save": (_int, [_vp, ctypes.c_char_p]),
@@ -369,6 +374,39 @@ def gfp_matvec_iterate(ctx: Context, p: int, A, x0, Y, iters: int, stream=None,
     _check(load().gfp_matvec_iterate(ctx.handle, p, n, _ptr(A), lda, _ptr(x0), _ptr(Y), iters,
                                      _stream(stream)), "gfp_matvec_iterate")
     return Y
+
+
+# ---- block products ----
+
+def gfp_matmul_block(ctx: Context, p: int, A, B, C, stream=None):
+    """C = A B mod p for 2-D device tensors (row strides become lda/ldb/ldc)."""
+    m, k = A.shape
+    k2, nb = B.shape
+    if k2 != k or tuple(C.shape) != (m, nb):
+        raise ValueError("shape mismatch")
+    for t, name in ((A, "A"), (B, "B"), (C, "C")):
+        if t.dtype.itemsize != 4 or t.stride(1) != 1:
+            raise ValueError(f"{name} must be a row-major 32-bit matrix")
+    _check(load().gfp_matmul_block(ctx.handle, p, m, k, nb, _ptr(A), A.stride(0), _ptr(B),
+                                   B.stride(0), _ptr(C), C.stride(0), _stream(stream)),
+           "gfp_matmul_block")
+    return C
+
+
+def gfp_matmul_block_csr(ctx: Context, p: int, k: int, row_ptr, col, val, B, C, stream=None):
+    m = row_ptr.numel() - 1
+    k2, nb = B.shape
+    if k2 != k or tuple(C.shape) != (m, nb):
+        raise ValueError("shape mismatch")
+    _check(load().gfp_matmul_block_csr(ctx.handle, p, m, k, nb, _ptr(row_ptr), _ptr(col), _ptr(val),
+                                       _ptr(B), B.stride(0), _ptr(C), C.stride(0), _stream(stream)),
+           "gfp_matmul_block_csr")
+    return C
+
+
+def gfp_context_check(ctx: Context) -> int:
+    """Synchronise; returns the status (GFP_OK, GFP_ERR_TIMEOUT, GFP_ERR_CUDA)."""
+    return int(load().gfp_context_check(ctx.handle))
 
 
 # ---- tuning ----

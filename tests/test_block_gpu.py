@@ -1,0 +1,163 @@
+"""Parity of the block products (tensor-core and CUDA-core dense paths, and
+the sparse-row path) with the oracle, bit for bit, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import gfp_inputs as gi
+import oracle
+from gpu_util import dev, dev2, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def fresh(ctx):
+    ctx.set_repr(0)
+    ctx.set_validate(False)
+    yield ctx
+    ctx.set_repr(0)
+    ctx.set_validate(False)
+    assert ctx is not None
+
+
+def run_block(lib, ctx, p, A, B, lda=None, ldb=None, ldc=None):
+    m, k = A.shape
+    nb = B.shape[1]
+    Ad, Bd = dev2(A, lda), dev2(B, ldb)
+    Cfull = torch.full((m, ldc or nb), -1, dtype=torch.int32, device="cuda")
+    Cd = Cfull[:, :nb]
+    lib.gfp_matmul_block(ctx, p, Ad, Bd, Cd)
+    torch.cuda.synchronize()
+    assert lib.gfp_context_check(ctx) == lib.GFP_OK
+    out = host(Cfull)
+    if ldc and ldc > nb:
+        assert (out[:, nb:] == 0xFFFFFFFF).all(), "wrote outside C"
+    return out[:, :nb]
+
+
+SHAPES_TC = [(1, 1, 1), (7, 13, 5), (128, 64, 64), (129, 1000, 64), (300, 2049, 70),
+             (64, 4101, 3), (257, 1025, 128), (130, 3000, 65)]
+
+
+@pytest.mark.parametrize("shape", SHAPES_TC)
+@pytest.mark.parametrize("p", [2, 3, 251, 32749, 65521, 65537, 65789])
+def test_block_tensor_core_parity(lib, fresh, p, shape):
+    fresh.set_repr(lib.GFP_REPR_F16TC)
+    m, k, nb = shape
+    A = gi.uniform(p, m * k, 61, 0).reshape(m, k)
+    B = gi.uniform(p, k * nb, 61, 1).reshape(k, nb)
+    lda = (k + 3) // 4 * 4   # the tensor-core path streams A rows with 16-byte loads
+    got = run_block(lib, fresh, p, A, B, lda=lda)
+    assert np.array_equal(got, oracle.block(p, A, B)), (p, shape)
+    # a row stride that is not a multiple of 4 cannot take the tensor-core path
+    if lda == k and k % 4 == 0:
+        with pytest.raises(lib.GfpError) as ei:
+            run_block(lib, fresh, p, A, B, lda=k + 1)
+        assert ei.value.status == lib.GFP_ERR_UNSUPPORTED
+
+
+def test_block_tensor_core_strides(lib, fresh):
+    fresh.set_repr(lib.GFP_REPR_F16TC)
+    p, m, k, nb = 65521, 200, 1500, 64
+    A = gi.uniform(p, m * k, 62, 0).reshape(m, k)
+    B = gi.uniform(p, k * nb, 62, 1).reshape(k, nb)
+    want = oracle.block(p, A, B)
+    for lda, ldb, ldc in ((k + 4, nb, nb), (k + 12, nb + 3, nb + 5)):
+        assert np.array_equal(run_block(lib, fresh, p, A, B, lda, ldb, ldc), want)
+
+
+@pytest.mark.parametrize("p", [65521, 65537, 65789])
+def test_block_tensor_core_extreme_digits(lib, fresh, p):
+    """Residues whose centred value is +-(p-1)/2 give digits of magnitude 128:
+    every 1024-term chunk of digit products reaches 2^24 exactly."""
+    fresh.set_repr(lib.GFP_REPR_F16TC)
+    h = (p - 1) // 2
+    m, k, nb = 256, 4096, 64
+    rng = np.random.default_rng(p)
+    A = np.where(rng.random((m, k)) < 0.5, h, p - h).astype(np.uint32)
+    B = np.where(rng.random((k, nb)) < 0.5, h, p - h).astype(np.uint32)
+    A[:, :1024] = h
+    B[:1024, :] = h
+    got = run_block(lib, fresh, p, A, B)
+    assert np.array_equal(got, oracle.block(p, A, B))
+    # all-equal case against the closed form k * h^2 mod p
+    A1 = np.full((128, 2048), h, np.uint32)
+    B1 = np.full((2048, 64), h, np.uint32)
+    assert (run_block(lib, fresh, p, A1, B1) == (2048 * h * h) % p).all()
+
+
+def test_block_auto_path_and_unsupported(lib, fresh):
+    p = 65521
+    A = gi.uniform(p, 50 * 70, 63, 0).reshape(50, 70)
+    B = gi.uniform(p, 70 * 9, 63, 1).reshape(70, 9)
+    assert np.array_equal(run_block(lib, fresh, p, A, B), oracle.block(p, A, B))
+    fresh.set_repr(lib.GFP_REPR_F16TC)
+    with pytest.raises(lib.GfpError) as ei:
+        run_block(lib, fresh, 2147483647, A, B)
+    assert ei.value.status == lib.GFP_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("repr_", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("p", [65521, 67108859, 2147483647, 4294967291])
+def test_block_cuda_core_parity(lib, fresh, p, repr_):
+    if repr_ == lib.GFP_REPR_FP64 and not lib.gfp_get_params(p)["fp64_ok"]:
+        pytest.skip("not eligible")
+    fresh.set_repr(repr_)
+    for m, k, nb in ((1, 1, 1), (65, 33, 64), (100, 700, 70), (3, 2000, 129)):
+        A = gi.uniform(p, m * k, 64, 0).reshape(m, k)
+        B = gi.uniform(p, k * nb, 64, 1).reshape(k, nb)
+        assert np.array_equal(run_block(lib, fresh, p, A, B, k + 1, nb + 2, nb + 1),
+                              oracle.block(p, A, B)), (m, k, nb)
+
+
+def test_block_k_zero_writes_zeros(lib, fresh):
+    A = torch.zeros((5, 4), dtype=torch.int32, device="cuda")[:, :0]
+    B = torch.zeros((0, 7), dtype=torch.int32, device="cuda")
+    C = torch.full((5, 7), -1, dtype=torch.int32, device="cuda")
+    lib.gfp_matmul_block(fresh, 65521, A, B, C)
+    torch.cuda.synchronize()
+    assert (host(C) == 0).all()
+
+
+def test_block_full_size_workload(lib, fresh):
+    """The block workload: A 16384 x 16384, B 16384 x 64 over GF(65521),
+    tensor-core path, every entry against the oracle."""
+    p, m, k, nb = 65521, 16384, 16384, 64
+    seed = gi.BASE_SEED + 3
+    A = gi.uniform(p, m * k, seed, 0).reshape(m, k)
+    B = gi.uniform(p, k * nb, seed, 1).reshape(k, nb)
+    got = run_block(lib, fresh, p, A, B)
+    want = oracle.block(p, A, B)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("repr_", [0, 1, 2, 3])
+def test_csr_parity(lib, fresh, repr_):
+    fresh.set_repr(repr_)
+    for p in (65521, 4294967291):
+        for m, k, nb, dens in ((1, 1, 1, 1.0), (50, 300, 64, 0.01), (200, 500, 70, 0.2),
+                               (33, 64, 130, 0.5)):
+            row_ptr, col, val = gi.csr_pattern(m, k, dens, p, seed=71)
+            B = gi.uniform(p, k * nb, 71, 9999).reshape(k, nb)
+            C = torch.full((m, nb), -1, dtype=torch.int32, device="cuda")
+            lib.gfp_matmul_block_csr(fresh, p, k, dev(row_ptr), dev(col) if col.size else dev(np.zeros(1, np.uint32)),
+                                     dev(val) if val.size else dev(np.zeros(1, np.uint32)), dev2(B), C)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(C), oracle.csr(p, row_ptr, col, val, B)), (p, m, k, nb)
+
+
+def test_csr_validation(lib, fresh):
+    p, m, k, nb = 65521, 10, 20, 8
+    row_ptr, col, val = gi.csr_pattern(m, k, 0.3, p, seed=72)
+    B = gi.uniform(p, k * nb, 72, 1).reshape(k, nb)
+    C = torch.zeros((m, nb), dtype=torch.int32, device="cuda")
+    fresh.set_validate(True)
+    bad = col.copy()
+    bad[0] = k   # column out of range
+    with pytest.raises(lib.GfpError) as ei:
+        lib.gfp_matmul_block_csr(fresh, p, k, dev(row_ptr), dev(bad), dev(val), dev2(B), C)
+    assert ei.value.status == lib.GFP_ERR_INVALID
+    lib.gfp_matmul_block_csr(fresh, p, k, dev(row_ptr), dev(col), dev(val), dev2(B), C)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(C), oracle.csr(p, row_ptr, col, val, B))
