@@ -96,6 +96,9 @@ typedef struct gfp_params {
 
 /* Static string naming a status code. */
 GFP_API const char *gfp_status_string(int status);
+/* Description of the last CUDA error that made an entry point of the calling
+ * thread return GFP_ERR_CUDA ("no CUDA error" if none). */
+GFP_API const char *gfp_last_cuda_error(void);
 
 /* Largest number of products lambda that an acc_bits-wide unsigned
  * accumulator can absorb before a reduction is required (Section 3.1,

@@ -26,9 +26,12 @@
 //
 // CUDA-core path (any p <= 2^32-1): shared-memory tiled product with the
 // per-thread unreduced accumulators of the dot-product kernels.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "gfp_internal.h"
 #include "gfp_tc.cuh"
@@ -41,18 +44,30 @@ constexpr int BK = 64;             // K per k-block: one 128-byte swizzle row of
 constexpr int NT = 64;             // output columns per n-tile
 constexpr int MMA_N = 2 * NT;      // hi and lo digits of B stacked along N
 constexpr int KC = 16;             // k-blocks per exact chunk (1024 terms)
-constexpr int STAGES = 4;
+#ifndef GFP_BLK_KB_PER_BOX
+#define GFP_BLK_KB_PER_BOX 1
+#endif
+#ifndef GFP_BLK_SA
+#define GFP_BLK_SA 3
+#endif
+constexpr int KBB = GFP_BLK_KB_PER_BOX;   // k-blocks per A box (longer row bursts for HBM)
+constexpr int SA = GFP_BLK_SA;            // A staging slots (uint32 boxes landed by TMA)
+constexpr int STAGES = 2;                 // digit stages (A hi, A lo, B) consumed by the MMAs
+constexpr int A_TILE_BYTES = BM * BK * 4 * KBB;               // 32 KiB of uint32 per k-block
 constexpr int A_DIGIT_BYTES = BM * BK * 2;                    // 16 KiB
 constexpr int B_TILE_BYTES = MMA_N * BK * 2;                  // 16 KiB
 constexpr int STAGE_BYTES = 2 * A_DIGIT_BYTES + B_TILE_BYTES; // 48 KiB
 constexpr int CONV_WARPS = 8;
 constexpr int EPI_WARPS = 4;
-constexpr int THREADS = 32 * (2 + CONV_WARPS + EPI_WARPS);   // 448
+constexpr int W_APROD = 0, W_MMA = 1, W_BPROD = 2, W_CONV0 = 3, W_EPI0 = W_CONV0 + CONV_WARPS;
+constexpr int THREADS = 32 * (W_EPI0 + EPI_WARPS);            // 480
 constexpr uint32_t TMEM_COLS = 512;   // 2 accumulator sets x 2 digits x 128 columns
 constexpr uint64_t WAIT_NS = 2000000000ull;   // bounded waits: 2 s
 constexpr uint32_t IDESC = ptx::idesc_f16_f32(BM, MMA_N);
 
 struct Bars {
+    uint64_t a_full[SA];       // uint32 A tile landed (1 arrival + tx bytes)
+    uint64_t a_empty[SA];      // A tile read by the converters (one arrival per converter warp)
     uint64_t full_b[STAGES];   // B digit tile landed (1 arrival + tx bytes)
     uint64_t full_a[STAGES];   // A digit tiles written (one arrival per converter warp)
     uint64_t empty[STAGES];    // MMAs reading the stage completed (tcgen05.commit)
@@ -63,11 +78,13 @@ struct Bars {
     uint32_t abort;
     uint32_t last_flag;
 };
-constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + (size_t)STAGES * STAGE_BYTES + 1024;
+constexpr size_t SMEM_BYTES =
+    1024 /*alignment slack*/ + (size_t)SA * A_TILE_BYTES + (size_t)STAGES * STAGE_BYTES + 1024;
+static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 
 struct Args {
-    const uint32_t *A;
-    uint64_t lda, m, k, nb;
+    CUtensorMap tmap_a;       // A as a 2-D uint32 tensor {k, m}, box {BK*KBB, BM}, zero fill
+    uint64_t m, k, nb;
     const uint8_t *Bimg;      // [n_tiles][kblocks] tiles of B_TILE_BYTES
     uint32_t *C;
     uint64_t ldc;
@@ -100,6 +117,15 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile
     }
 }
 
+// warp-uniform bounded wait: lane 0 polls, the result is broadcast
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile uint32_t *abort,
+                                          uint32_t *err)
+{
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) ok = wait_bar(bar, parity, abort, err);
+    return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
 struct UnitPos {
     uint32_t nt, mt, c, kb0, kb1;
 };
@@ -116,53 +142,32 @@ __device__ __forceinline__ UnitPos unit_pos(const Args &a, uint64_t u)
     return q;
 }
 
-// Centre a residue and split it into two balanced 8-bit digits (fp16 pair).
-__device__ __forceinline__ void split_digits(uint32_t a, uint32_t p, uint32_t half, __half &h,
-                                             __half &l)
+// Centre two residues and split each into balanced 8-bit digits, returned
+// as packed fp16 pairs (element 0 in the low half).  With u = s + 32896, where
+// s in [-32895, 32895] is the centred residue, the digits of s = 256 h + l are
+// l = (u & 255) - 128 and h = (u >> 8) - 128.  The fp16 encoding of 1536 + d
+// for an integer |d| <= 512 is the 16-bit integer 0x6600 + d (exponent of
+// [1024, 2048), unit spacing), so a byte permute plus one integer add builds
+// 1536 + d for both lanes and one exact fp16 subtraction leaves d.
+__device__ __forceinline__ void split_pair(uint32_t a0, uint32_t a1, uint32_t p, uint32_t half,
+                                           uint32_t &hi2, uint32_t &lo2)
 {
-    const int s = (a > half) ? (int)a - (int)p : (int)a;
-    const int lo = ((s + 128) & 255) - 128;
-    const int hi = (s - lo) >> 8;
-    h = __int2half_rn(hi);
-    l = __int2half_rn(lo);
+    const uint32_t u0 = a0 + 32896u - (a0 > half ? p : 0u);
+    const uint32_t u1 = a1 + 32896u - (a1 > half ? p : 0u);
+    const uint32_t lo_bits = __byte_perm(u0, u1, 0x3430) + 0x65806580u;   // [u0 & 255, u1 & 255]
+    const uint32_t hi_bits = __byte_perm(u0, u1, 0x6521) + 0x65806580u;   // [u0 >> 8, u1 >> 8]
+    const __half2 bias = __halves2half2(__ushort_as_half(0x6600), __ushort_as_half(0x6600));
+    const __half2 lo = __hsub2(*reinterpret_cast<const __half2 *>(&lo_bits), bias);
+    const __half2 hi = __hsub2(*reinterpret_cast<const __half2 *>(&hi_bits), bias);
+    lo2 = *reinterpret_cast<const uint32_t *>(&lo);
+    hi2 = *reinterpret_cast<const uint32_t *>(&hi);
 }
 
-__device__ __forceinline__ uint32_t pack2(__half a, __half b)
-{
-    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
-}
-
-// A tile loader of one converter thread: 8 chunks of 4 consecutive K of one row.
-struct ATileRegs {
-    uint4 v[8];
-};
-
-__device__ __forceinline__ void load_a_tile(const Args &a, uint32_t mt, uint32_t kb, int ct,
-                                            ATileRegs &r)
-{
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int q = ct + 256 * i;
-        const int row = q >> 4, c4 = q & 15;
-        const uint64_t gr = (uint64_t)mt * BM + row;
-        const uint64_t gc = (uint64_t)kb * BK + (uint64_t)c4 * 4;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (gr < a.m) {
-            const uint32_t *src = a.A + gr * a.lda + gc;
-            if (gc + 3 < a.k) {
-                v = __ldcs(reinterpret_cast<const uint4 *>(src));
-            } else {
-                if (gc + 0 < a.k) v.x = __ldcs(src + 0);
-                if (gc + 1 < a.k) v.y = __ldcs(src + 1);
-                if (gc + 2 < a.k) v.z = __ldcs(src + 2);
-            }
-        }
-        r.v[i] = v;
-    }
-}
-
-__device__ __forceinline__ void store_a_digits(const Args &a, uint8_t *stage, int ct,
-                                               const ATileRegs &r)
+// Converter thread ct (0..255): 8 chunks of 4 consecutive K of one row, read
+// from the landed uint32 tile (row-major, 256 bytes per row) and written as
+// digits into the two 128-byte-swizzled K-major fp16 tiles of a stage.
+__device__ __forceinline__ void convert_tile(const Args &a, const uint8_t *atile, uint8_t *stage,
+                                             int ct, int sub)
 {
     uint8_t *th = stage;                    // high digits
     uint8_t *tl = stage + A_DIGIT_BYTES;    // low digits
@@ -170,30 +175,36 @@ __device__ __forceinline__ void store_a_digits(const Args &a, uint8_t *stage, in
     for (int i = 0; i < 8; ++i) {
         const int q = ct + 256 * i;
         const int row = q >> 4, c4 = q & 15;
-        __half h0, h1, h2, h3, l0, l1, l2, l3;
-        split_digits(r.v[i].x, a.mod.p, a.half, h0, l0);
-        split_digits(r.v[i].y, a.mod.p, a.half, h1, l1);
-        split_digits(r.v[i].z, a.mod.p, a.half, h2, l2);
-        split_digits(r.v[i].w, a.mod.p, a.half, h3, l3);
+        const uint4 v =
+            *reinterpret_cast<const uint4 *>(atile + row * (BK * 4 * KBB) + sub * (BK * 4) + c4 * 16);
+        uint32_t h01, l01, h23, l23;
+        split_pair(v.x, v.y, a.mod.p, a.half, h01, l01);
+        split_pair(v.z, v.w, a.mod.p, a.half, h23, l23);
         // 128-byte swizzle: 16-byte chunk j of row r sits at chunk j ^ (r & 7)
         const int j = c4 >> 1, halfsel = c4 & 1;
         const uint32_t off = (uint32_t)row * 128u + ((uint32_t)(j ^ (row & 7)) << 4) + (halfsel << 3);
-        *reinterpret_cast<uint2 *>(th + off) = make_uint2(pack2(h0, h1), pack2(h2, h3));
-        *reinterpret_cast<uint2 *>(tl + off) = make_uint2(pack2(l0, l1), pack2(l2, l3));
+        *reinterpret_cast<uint2 *>(th + off) = make_uint2(h01, h23);
+        *reinterpret_cast<uint2 *>(tl + off) = make_uint2(l01, l23);
     }
 }
 
-__global__ void __launch_bounds__(THREADS, 1) k_block_tc(Args a)
+__global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__ Args a)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    Bars *bars = reinterpret_cast<Bars *>(smem + (size_t)STAGES * STAGE_BYTES);
+    uint8_t *stg = smem;                                      // SA uint32 A tiles
+    uint8_t *dig = smem + (size_t)SA * A_TILE_BYTES;          // STAGES digit stages
+    Bars *bars = reinterpret_cast<Bars *>(dig + (size_t)STAGES * STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const uint64_t u0 = a.units * blockIdx.x / gridDim.x;
     const uint64_t u1 = a.units * (blockIdx.x + 1) / gridDim.x;
 
     if (threadIdx.x == 0) {
+        for (int s = 0; s < SA; ++s) {
+            ptx::mbar_init(ptx::smem_u32(&bars->a_full[s]), 1);
+            ptx::mbar_init(ptx::smem_u32(&bars->a_empty[s]), CONV_WARPS);
+        }
         for (int s = 0; s < STAGES; ++s) {
             ptx::mbar_init(ptx::smem_u32(&bars->full_b[s]), 1);
             ptx::mbar_init(ptx::smem_u32(&bars->full_a[s]), CONV_WARPS);
@@ -208,7 +219,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(Args a)
         bars->last_flag = 0;
         ptx::fence_barrier_init();
     }
-    if (warp == 1) {
+    if (warp == W_MMA) {
         ptx::tmem_alloc(ptx::smem_u32(&bars->tmem_base), TMEM_COLS);
         ptx::tmem_relinquish();
     }
@@ -218,16 +229,49 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(Args a)
     const uint32_t tmem = bars->tmem_base;
     volatile uint32_t *abort = &bars->abort;
 
-    if (warp == 0) {
-        // ---------------- B digit tiles: bulk copies ----------------
+    if (warp == W_APROD) {
+        // ---------------- producer: uint32 A boxes (TMA, KBB k-blocks each) ----------------
         if (lane == 0) {
-            uint32_t it = 0;
+            int armed[SA];
+            for (int s = 0; s < SA; ++s) armed[s] = -1;
+            uint32_t bi = 0;
+            bool ok = true;
+            ptx::prefetch_tensormap(&a.tmap_a);
+            for (uint64_t u = u0; u < u1 && ok; ++u) {
+                const UnitPos q = unit_pos(a, u);
+                for (uint32_t kb = q.kb0; kb < q.kb1; kb += KBB, ++bi) {
+                    const uint32_t s = bi % SA, round = bi / SA;
+                    if (round > 0 &&
+                        !wait_bar(ptx::smem_u32(&bars->a_empty[s]), (round - 1) & 1, abort, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = ptx::smem_u32(&bars->a_full[s]);
+                    ptx::mbar_arrive_expect_tx(fb, A_TILE_BYTES);
+                    ptx::tma_load_2d(ptx::smem_u32(stg + (size_t)s * A_TILE_BYTES), &a.tmap_a,
+                                     (int)(kb * BK), (int)(q.mt * BM), fb);
+                    armed[s] = (int)round;
+                }
+            }
+            // copies already issued must land before the CTA can exit
+            for (int s = 0; s < SA; ++s) {
+                if (armed[s] < 0) continue;
+                const uint32_t fb = ptx::smem_u32(&bars->a_full[s]);
+                const uint64_t t0 = ptx::globaltimer();
+                while (!ptx::mbar_try_wait(fb, armed[s] & 1) && ptx::globaltimer() - t0 < WAIT_NS) {
+                }
+            }
+        }
+    } else if (warp == W_BPROD) {
+        // ---------------- producer: B digit tiles (bulk copies from the prepared image) ----------------
+        if (lane == 0) {
             int armed[STAGES];
             for (int s = 0; s < STAGES; ++s) armed[s] = -1;
+            uint32_t it = 0;
             bool ok = true;
             for (uint64_t u = u0; u < u1 && ok; ++u) {
                 const UnitPos q = unit_pos(a, u);
-                for (uint32_t kb = q.kb0; kb < q.kb1 && ok; ++kb, ++it) {
+                for (uint32_t kb = q.kb0; kb < q.kb1; ++kb, ++it) {
                     const uint32_t s = it % STAGES, round = it / STAGES;
                     if (round > 0 &&
                         !wait_bar(ptx::smem_u32(&bars->empty[s]), (round - 1) & 1, abort, a.err)) {
@@ -236,24 +280,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(Args a)
                     }
                     const uint32_t fb = ptx::smem_u32(&bars->full_b[s]);
                     ptx::mbar_arrive_expect_tx(fb, B_TILE_BYTES);
-                    ptx::bulk_g2s(ptx::smem_u32(smem + (size_t)s * STAGE_BYTES + 2 * A_DIGIT_BYTES),
+                    ptx::bulk_g2s(ptx::smem_u32(dig + (size_t)s * STAGE_BYTES + 2 * A_DIGIT_BYTES),
                                   a.Bimg + ((uint64_t)q.nt * a.kblocks + kb) * B_TILE_BYTES,
                                   B_TILE_BYTES, fb);
                     armed[s] = (int)round;
                 }
             }
-            if (!ok) {
-                // let copies already issued land before the CTA can exit
-                for (int s = 0; s < STAGES; ++s) {
-                    if (armed[s] < 0) continue;
-                    const uint64_t t0 = ptx::globaltimer();
-                    while (!ptx::mbar_try_wait(ptx::smem_u32(&bars->full_b[s]), armed[s] & 1) &&
-                           ptx::globaltimer() - t0 < WAIT_NS) {
-                    }
+            for (int s = 0; s < STAGES; ++s) {
+                if (armed[s] < 0) continue;
+                const uint32_t fb = ptx::smem_u32(&bars->full_b[s]);
+                const uint64_t t0 = ptx::globaltimer();
+                while (!ptx::mbar_try_wait(fb, armed[s] & 1) && ptx::globaltimer() - t0 < WAIT_NS) {
                 }
             }
         }
-    } else if (warp == 1) {
+    } else if (warp == W_MMA) {
         // ---------------- MMA issue (one thread) ----------------
         if (lane == 0) {
             uint32_t it = 0;
@@ -278,7 +319,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(Args a)
                         break;
                     }
                     ptx::tc_fence_after();
-                    const uint32_t base = ptx::smem_u32(smem + (size_t)s * STAGE_BYTES);
+                    const uint32_t base = ptx::smem_u32(dig + (size_t)s * STAGE_BYTES);
                     const uint64_t dah = ptx::sdesc_k_sw128(base);
                     const uint64_t dal = ptx::sdesc_k_sw128(base + A_DIGIT_BYTES);
                     const uint64_t db = ptx::sdesc_k_sw128(base + 2 * A_DIGIT_BYTES);
@@ -301,52 +342,36 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(Args a)
                    ptx::globaltimer() - t0 < WAIT_NS) {
             }
         }
-    } else if (warp < 2 + CONV_WARPS) {
-        // ---------------- A: HBM -> centred fp16 digits in shared memory ----------------
-        const int ct = threadIdx.x - 64;   // 0..255
-        const int cw = warp - 2;
-        uint32_t it = 0;
-        // (unit, k-block) sequence with one tile of register prefetch
-        uint64_t u = u0;
-        UnitPos q;
-        uint32_t kb = 0;
-        if (u < u1) {
-            q = unit_pos(a, u);
-            kb = q.kb0;
-        }
-        ATileRegs cur, nxt;
-        if (u < u1) load_a_tile(a, q.mt, kb, ct, cur);
-        while (u < u1) {
-            // position of the next tile
-            uint64_t nu = u;
-            UnitPos nq = q;
-            uint32_t nkb = kb + 1;
-            if (nkb >= q.kb1) {
-                ++nu;
-                if (nu < u1) {
-                    nq = unit_pos(a, nu);
-                    nkb = nq.kb0;
+    } else if (warp < W_EPI0) {
+        // ---------------- converters: uint32 tile -> centred fp16 digits ----------------
+        const int ct = threadIdx.x - 32 * W_CONV0;   // 0..255
+        uint32_t it = 0, bi = 0;
+        bool ok = true;
+        for (uint64_t u = u0; u < u1 && ok; ++u) {
+            const UnitPos q = unit_pos(a, u);
+            for (uint32_t kb = q.kb0; kb < q.kb1 && ok; kb += KBB, ++bi) {
+                const uint32_t sa = bi % SA, ra = bi / SA;
+                if (!warp_wait(ptx::smem_u32(&bars->a_full[sa]), ra & 1, abort, a.err)) {
+                    ok = false;
+                    break;
                 }
+                const uint32_t nsub = min((uint32_t)KBB, q.kb1 - kb);
+                for (uint32_t sub = 0; sub < nsub; ++sub, ++it) {
+                    const uint32_t s = it % STAGES, round = it / STAGES;
+                    if (round > 0 &&
+                        !warp_wait(ptx::smem_u32(&bars->empty[s]), (round - 1) & 1, abort, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    convert_tile(a, stg + (size_t)sa * A_TILE_BYTES, dig + (size_t)s * STAGE_BYTES, ct,
+                                 (int)sub);
+                    ptx::fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&bars->full_a[s]));
+                }
+                if (!ok) break;
+                if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&bars->a_empty[sa]));
             }
-            if (nu < u1) load_a_tile(a, nq.mt, nkb, ct, nxt);
-            const uint32_t s = it % STAGES, round = it / STAGES;
-            bool ok = true;
-            if (round > 0) {
-                if (lane == 0)
-                    ok = wait_bar(ptx::smem_u32(&bars->empty[s]), (round - 1) & 1, abort, a.err);
-                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-            }
-            if (!ok) break;
-            store_a_digits(a, smem + (size_t)s * STAGE_BYTES, ct, cur);
-            ptx::fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&bars->full_a[s]));
-            (void)cw;
-            ++it;
-            u = nu;
-            q = nq;
-            kb = nkb;
-            cur = nxt;
         }
     } else {
         // ---------------- epilogue: TMEM -> residues ----------------
@@ -358,18 +383,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(Args a)
         for (int j = 0; j < NT; ++j) res[j] = 0;
         uint32_t seg_chunks = 0;
         uint64_t idx = 0;
-        bool ok = true;
-        for (uint64_t u = u0; u < u1 && ok; ++u, ++idx) {
+        for (uint64_t u = u0; u < u1; ++u, ++idx) {
             const UnitPos q = unit_pos(a, u);
             const uint32_t b = (uint32_t)(idx & 1), use = (uint32_t)(idx >> 1);
-            bool got = true;
-            if (lane == 0) got = wait_bar(ptx::smem_u32(&bars->acc_full[b]), use & 1, abort, a.err);
-            got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+            const bool got = warp_wait(ptx::smem_u32(&bars->acc_full[b]), use & 1, abort, a.err);
             // decide together: the epilogue warps meet at named barriers below
-            if (ptx::bar_red_or<1, EPI_WARPS * 32>(!got || *abort != 0)) {
-                ok = false;
-                break;
-            }
+            if (ptx::bar_red_or<1, EPI_WARPS * 32>(!got || *abort != 0)) break;
             ptx::tc_fence_after();
             const uint32_t d_hi = tmem + lane_bits + b * 256u;
             const uint32_t d_lo = d_hi + 128u;
@@ -414,9 +433,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(Args a)
                 for (int j = 0; j < NT; ++j) res[j] = 0;
                 __threadfence();
                 asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32));
-                if (warp == 2 + CONV_WARPS && lane == 0) {
-                    const uint32_t t = a.n_tiles > 0 ? q.nt * a.m_tiles + q.mt : 0;
-                    const uint32_t old = atomicAdd(&a.tickets[t], seg_chunks);
+                if (warp == W_EPI0 && lane == 0) {
+                    const uint32_t old = atomicAdd(&a.tickets[q.nt * a.m_tiles + q.mt], seg_chunks);
                     bars->last_flag = (old + seg_chunks == a.chunks) ? 1u : 0u;
                     __threadfence();
                 }
@@ -431,7 +449,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(Args a)
                         }
                     }
                     asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32));
-                    if (warp == 2 + CONV_WARPS && lane == 0) {
+                    if (warp == W_EPI0 && lane == 0) {
                         atomicExch(&a.tickets[q.nt * a.m_tiles + q.mt], 0u);
                         bars->last_flag = 0;
                     }
@@ -444,7 +462,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(Args a)
 
     ptx::tc_fence_before();
     __syncthreads();
-    if (warp == 1) {
+    if (warp == W_MMA) {
         ptx::tc_fence_after();
         ptx::tmem_dealloc(tmem, TMEM_COLS);
     }
@@ -462,19 +480,17 @@ __global__ void k_block_prep_b(const uint32_t *B, uint64_t ldb, uint64_t k, uint
     for (int t = threadIdx.x; t < 64 * 8; t += blockDim.x) {
         const int col = t >> 3, j = t & 7;       // output column within the tile, 16-byte chunk
         const uint64_t gcol = (uint64_t)nt * NT + col;
-        __half hi[8], lo[8];
+        uint32_t v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const uint64_t gk = (uint64_t)kb * BK + j * 8 + e;
-            uint32_t v = 0;
-            if (gk < k && gcol < nb) v = B[gk * ldb + gcol];
-            split_digits(v, mod.p, half, hi[e], lo[e]);
+            v[e] = (gk < k && gcol < nb) ? B[gk * ldb + gcol] : 0u;
         }
         uint4 wh, wl;
-        wh.x = pack2(hi[0], hi[1]); wh.y = pack2(hi[2], hi[3]);
-        wh.z = pack2(hi[4], hi[5]); wh.w = pack2(hi[6], hi[7]);
-        wl.x = pack2(lo[0], lo[1]); wl.y = pack2(lo[2], lo[3]);
-        wl.z = pack2(lo[4], lo[5]); wl.w = pack2(lo[6], lo[7]);
+        split_pair(v[0], v[1], mod.p, half, wh.x, wl.x);
+        split_pair(v[2], v[3], mod.p, half, wh.y, wl.y);
+        split_pair(v[4], v[5], mod.p, half, wh.z, wl.z);
+        split_pair(v[6], v[7], mod.p, half, wh.w, wl.w);
         const int rh = col, rl = col + 64;
         *reinterpret_cast<uint4 *>(out + rh * 128 + ((j ^ (rh & 7)) << 4)) = wh;
         *reinterpret_cast<uint4 *>(out + rl * 128 + ((j ^ (rl & 7)) << 4)) = wl;
@@ -580,6 +596,22 @@ uint32_t *block_tc_err_flag(void *ws, uint64_t m, uint64_t k, uint64_t nb)
     return (uint32_t *)((uint8_t *)ws + block_tc_workspace_bytes(m, k, nb) - 256);
 }
 
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
 cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb, const uint32_t *A,
                             uint64_t lda, const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc,
                             void *ws, int sm_count, cudaStream_t s, int *launches)
@@ -592,9 +624,19 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return cudaErrorNotSupported;
     Args a;
-    a.A = A;
-    a.lda = lda;
+    memset(&a, 0, sizeof a);
+    // A: innermost dimension k (elements), then m rows lda*4 bytes apart
+    const cuuint64_t gdim[2] = {(cuuint64_t)k, (cuuint64_t)m};
+    const cuuint64_t gstride[1] = {(cuuint64_t)lda * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)(BK * KBB), (cuuint32_t)BM};
+    const cuuint32_t estride[2] = {1, 1};
+    if (encode(&a.tmap_a, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, (void *)A, gdim, gstride, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     a.m = m;
     a.k = k;
     a.nb = nb;

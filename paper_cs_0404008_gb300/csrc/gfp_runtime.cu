@@ -72,10 +72,16 @@ using namespace gfp;
 // helpers
 // ---------------------------------------------------------------------------
 
+// The last CUDA error seen by an entry point of this thread (diagnostics).
+static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
 #define GFP_CUDA_TRY(expr)                                   \
     do {                                                     \
         cudaError_t e_ = (expr);                             \
-        if (e_ != cudaSuccess) return GFP_ERR_CUDA;          \
+        if (e_ != cudaSuccess) {                             \
+            g_last_cuda_error = e_;                          \
+            return GFP_ERR_CUDA;                             \
+        }                                                    \
     } while (0)
 
 static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -298,6 +304,11 @@ GFP_API const char *gfp_status_string(int st)
     case GFP_ERR_CANCELLED: return "GFP_ERR_CANCELLED";
     default: return "GFP_UNKNOWN_STATUS";
     }
+}
+
+GFP_API const char *gfp_last_cuda_error(void)
+{
+    return g_last_cuda_error == cudaSuccess ? "no CUDA error" : cudaGetErrorString(g_last_cuda_error);
 }
 
 GFP_API uint64_t gfp_delay_bound(uint32_t p, int acc_bits, int carried)

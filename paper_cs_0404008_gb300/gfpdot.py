@@ -43,7 +43,10 @@ _int = ctypes.c_int
 class GfpError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
-        super().__init__(f"{where}: {gfp_status_string(status)} ({status})")
+        msg = f"{where}: {gfp_status_string(status)} ({status})"
+        if status == GFP_ERR_CUDA:
+            msg += f": {load().gfp_last_cuda_error().decode()}"
+        super().__init__(msg)
 
 
 class gfp_params(ctypes.Structure):
@@ -57,6 +60,7 @@ class gfp_dot_desc(ctypes.Structure):
 
 _SIGS = {
     "gfp_status_string": (ctypes.c_char_p, [_int]),
+    "gfp_last_cuda_error": (ctypes.c_char_p, []),
     "gfp_delay_bound": (_u64, [_u32, _int, _int]),
     "gfp_get_params": (_int, [_u32, ctypes.POINTER(gfp_params)]),
     "gfp_reduce_u64": (_u32, [_u64, _u32]),
