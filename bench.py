@@ -591,6 +591,175 @@ def run_secondary(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# serving: Poisson stream of mixed jobs through the continuous-batching server
+# ---------------------------------------------------------------------------
+
+def serve_requests(count: int, seed: int):
+    """Seeded request mix: 70% dot (n log-uniform [2^10, 2^22]), 25% matvec,
+    5% block over pools of 16 registered matrices per kind; primes uniform over
+    {65521, 67108859, 4294967291}."""
+    u = gi.unit_doubles(seed, 10, count)
+    v = gi.unit_doubles(seed, 11, count)
+    w = gi.words(seed, 12, count)
+    kinds = np.where(u < 0.70, 0, np.where(u < 0.95, 1, 2))
+    reqs = []
+    for i in range(count):
+        k = int(kinds[i])
+        if k == 0:
+            n = int(np.floor(2.0 ** (10 + 12 * v[i])))
+            reqs.append((0, gi.PRIMES_SERVE[int(w[i] % np.uint64(3))], n, 0, seed * 1000003 + i))
+        else:
+            reqs.append((k, None, 0, int(w[i] % np.uint64(16)), seed * 1000003 + i))
+    return reqs
+
+
+def run_serve(args):
+    import threading as th
+    import torch
+    from paper_cs_0404008_gb300 import gfpdot as g
+    import oracle
+
+    torch.cuda.set_device(0)
+    g.load()
+    seed = gi.BASE_SEED + 5
+    srv = g.Server(device=0, mem_budget=16 << 30, n_streams=8, batch_window_us=50,
+                   max_inflight=256)
+    # resident matrix pools (registered once): sides log-uniform
+    pools = {1: [], 2: []}
+    for kind, lo, hi in ((1, 10, 14), (2, 10, 13)):
+        du = gi.unit_doubles(seed, 20 + kind, 16)
+        dw = gi.words(seed, 22 + kind, 16)
+        for i in range(16):
+            side = int(np.floor(2.0 ** (lo + (hi - lo) * du[i])))
+            p = gi.PRIMES_SERVE[int(dw[i] % np.uint64(3))]
+            mseed = seed * 7919 + kind * 100 + i
+            h = srv.register_matrix(p, side, side, seed=mseed)
+            pools[kind].append((h, p, side, mseed))
+    reqs = serve_requests(args.requests, seed)
+
+    def submit(r):
+        k, p, n, mi, sd = r
+        if k == 0:
+            return srv.submit(g.GFP_JOB_DOT, p, n=n, seed=sd)
+        h, mp, side, _ = pools[k][mi]
+        if k == 1:
+            return srv.submit(g.GFP_JOB_MATVEC, mp, matrix=h, seed=sd)
+        return srv.submit(g.GFP_JOB_BLOCK, mp, matrix=h, nb=64, seed=sd)
+
+    def macs(r):
+        k, p, n, mi, sd = r
+        if k == 0:
+            return float(n)
+        side = pools[k][mi][2]
+        return float(side) * side * (64 if k == 2 else 1)
+
+    # warm-up and capacity: a closed burst
+    burst = reqs[:min(2000, len(reqs))]
+    for r in burst[:50]:
+        st, _ = srv.wait(submit(r))
+    t0 = time.perf_counter()
+    tks = [submit(r) for r in burst]
+    for t in tks:
+        st, res = srv.wait(t)
+        srv.release(t)
+    cap = len(burst) / (time.perf_counter() - t0)
+    lam = args.load * cap
+
+    # open-loop Poisson arrivals
+    gaps = -np.log1p(-gi.unit_doubles(seed, 30, len(reqs))) / lam
+    sample = set(range(0, len(reqs), 100))           # 1% verified against the oracle
+    results = [None] * len(reqs)
+    outs = {}
+    tickets = [None] * len(reqs)
+    ready = th.Semaphore(0)
+
+    def collector():
+        for i in range(len(reqs)):
+            ready.acquire()
+            st, res = srv.wait(tickets[i], 600_000_000)
+            results[i] = (st, res.status, res.value, res.t_submit_ns, res.t_done_ns, res.batch)
+            if i in sample and res.status == g.GFP_OK and reqs[i][0] != 0:
+                outs[i] = srv.result_copy(tickets[i], res.out_elems)
+            srv.release(tickets[i])
+
+    col = th.Thread(target=collector, daemon=True)
+    col.start()
+    stats0 = srv.stats()
+    t_start = time.perf_counter()
+    t_next = t_start
+    for i, r in enumerate(reqs):
+        t_next += gaps[i]
+        while True:
+            d = t_next - time.perf_counter()
+            if d <= 0:
+                break
+            if d > 2e-4:
+                time.sleep(d - 1e-4)
+        tickets[i] = submit(r)
+        ready.release()
+    col.join()
+    wall = time.perf_counter() - t_start
+    stats1 = srv.stats()
+    lat = np.array([(x[4] - x[3]) / 1e6 for x in results])
+    ok = all(x[0] == g.GFP_OK and x[1] == g.GFP_OK for x in results)
+    total_macs = sum(macs(r) for r in reqs)
+
+    # verification: sampled results against the oracle (matrices regenerated
+    # on the host from their seeds), and a replay alone
+    bad = 0
+    checked = 0
+    for i in sorted(sample):
+        k, p, n, mi, sd = reqs[i]
+        if k == 0:
+            want = oracle.dot(p, gi.uniform(p, n, sd, 0), gi.uniform(p, n, sd, 1))
+            bad += int(results[i][2] != want)
+            checked += 1
+        else:
+            h, mp, side, mseed = pools[k][mi]
+            if side > 3000:
+                continue    # keep host verification bounded
+            A = gi.uniform(mp, side * side, mseed, 0).reshape(side, side)
+            if k == 1:
+                want = oracle.matvec(mp, A, gi.uniform(mp, side, sd, 0))
+            else:
+                want = oracle.block(mp, A, gi.uniform(mp, side * 64, sd, 0).reshape(side, 64)).ravel()
+            bad += int(not np.array_equal(outs[i], want))
+            checked += 1
+    replay_bad = 0
+    for i in sorted(sample)[:20]:
+        t = submit(reqs[i])
+        st, res = srv.wait(t)
+        if reqs[i][0] == 0:
+            replay_bad += int(res.value != results[i][2])
+        elif i in outs:
+            replay_bad += int(not np.array_equal(srv.result_copy(t, res.out_elems), outs[i]))
+        srv.release(t)
+    srv.close()
+    line = {
+        "metric": METRIC, "value": total_macs / wall / 1e9, "unit": UNIT, "n_gpus": 1,
+        "steps": 1, "warmup": 50, "ms_per_step": wall * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"serving: Poisson stream of {len(reqs)} requests, 70% dot "
+                               "(n log-uniform [2^10,2^22]), 25% matvec (16 resident square "
+                               "matrices, side log-uniform [2^10,2^14]), 5% block (16 resident "
+                               "m=k log-uniform [2^10,2^13], nb=64), p uniform over {65521, "
+                               "67108859, 4294967291}, server-generated operands",
+                   "load": args.load},
+        "serve": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                  "mean_ms": float(lat.mean()), "capacity_jobs_per_s": cap,
+                  "lambda_jobs_per_s": lam, "achieved_jobs_per_s": len(reqs) / wall,
+                  "all_ok": bool(ok), "verified": checked, "verify_mismatches": bad,
+                  "replayed_alone": min(20, len(sample)), "replay_mismatches": replay_bad,
+                  "admission_stalls": stats1["admission_stalls"] - stats0["admission_stalls"],
+                  "dot_launches": stats1["dot_launches"] - stats0["dot_launches"],
+                  "mean_dot_batch": float(np.mean([x[5] for x, r in zip(results, reqs) if r[0] == 0])),
+                  "mem_peak_bytes": stats1["mem_peak"]},
+        "gpu_launches": stats1["kernel_launches"] - stats0["kernel_launches"],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -604,7 +773,9 @@ def main():
     ap.add_argument("--no-clocks", action="store_true", help="skip the clock-sampling load phase")
     ap.add_argument("--pairs", type=int, default=COUNT, help="batch size (smaller for profiling)")
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "dot", "matvec", "block", "csr"])
+                    choices=["batched", "dot", "matvec", "block", "csr", "serve"])
+    ap.add_argument("--requests", type=int, default=20000, help="serve: Poisson requests")
+    ap.add_argument("--load", type=float, default=0.7, help="serve: arrival rate / capacity")
     ap.add_argument("--block-m", type=int, default=16384, help="block workload rows (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -613,6 +784,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_gpu(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_secondary(args)
 

@@ -284,6 +284,91 @@ GFP_API gfp_status gfp_plan_save(const gfp_ctx *ctx, const char *path);
 /* Number of (p, length bucket) entries in the context's plan. */
 GFP_API uint64_t gfp_plan_size(const gfp_ctx *ctx);
 
+/* ---- service: continuous batching of dot, matrix-vector and block jobs ---- */
+
+typedef struct gfp_server gfp_server;
+
+typedef enum gfp_job_kind { GFP_JOB_DOT = 0, GFP_JOB_MATVEC = 1, GFP_JOB_BLOCK = 2 } gfp_job_kind;
+
+typedef struct gfp_server_cfg {
+    int device;                 /* CUDA device */
+    uint64_t mem_budget;        /* device bytes for job operands and results (0: 4 GiB) */
+    uint32_t max_inflight;      /* launches on the GPU at once; a batched dot launch counts once (0: 256) */
+    uint32_t n_streams;         /* stream pool size (0: 4) */
+    uint32_t queue_capacity;    /* submitted but not admitted jobs before GFP_ERR_AGAIN (0: 65536) */
+    uint32_t batch_window_us;   /* dot jobs arriving within this window share one launch (0: none) */
+    uint32_t simulate;          /* 1: no GPU; jobs "run" on the host for a time proportional to
+                                   their work (scheduling, admission and API tests without a GPU) */
+    uint32_t fail_every;        /* fault injection: every n-th admission attempt fails as if the
+                                   device allocation failed (0: off) */
+} gfp_server_cfg;
+
+/* A job.  Operands are either caller device pointers (which must stay valid
+ * until the job completes) or, when a pointer is NULL, generated by the server
+ * in its own memory with gfp_fill_uniform(p, seed, stream, 0, ...), stream 0
+ * for x / the vector / B and stream 1 for y.
+ *   DOT:    n, x, y.  The residue is returned in gfp_result.value.
+ *   MATVEC: matrix (handle of a registered rows x cols matrix), v (cols).
+ *           Output: rows residues in server memory.
+ *   BLOCK:  matrix (m x k), v = B (k x nb, row-major), nb.  Output m x nb.
+ * Outputs of MATVEC and BLOCK stay in server memory (counted against the
+ * budget) until gfp_release; read them with gfp_result_copy. */
+typedef struct gfp_job {
+    uint32_t kind;
+    uint32_t p;
+    uint64_t n;
+    uint64_t nb;
+    uint64_t matrix;
+    const uint32_t *x;
+    const uint32_t *y;
+    const uint32_t *v;
+    uint64_t seed;
+} gfp_job;
+
+typedef struct gfp_result {
+    int32_t status;             /* GFP_OK, GFP_ERR_* of the job */
+    uint32_t kind;
+    uint32_t value;             /* DOT: the residue */
+    uint32_t batch;             /* DOT: number of dot jobs that shared its launch */
+    uint64_t out_elems;         /* MATVEC / BLOCK: output residues held for gfp_result_copy */
+    uint64_t t_submit_ns, t_admit_ns, t_start_ns, t_done_ns;   /* CLOCK_MONOTONIC */
+} gfp_result;
+
+typedef struct gfp_server_stats {
+    uint64_t submitted, admitted, completed, failed, cancelled;
+    uint64_t admission_stalls;  /* dispatcher passes that left a job waiting for memory or a slot */
+    uint64_t dot_launches;      /* batched launches carrying dot jobs */
+    uint64_t mem_in_use, mem_peak, mem_budget;
+    uint64_t kernel_launches;
+} gfp_server_stats;
+
+/* Start a server: allocates the memory budget as one device arena, the stream
+ * pool and one context per stream, and starts the dispatcher thread. */
+GFP_API gfp_status gfp_server_create(const gfp_server_cfg *cfg, gfp_server **out);
+/* Stop the dispatcher, cancel jobs not yet admitted (GFP_ERR_CANCELLED),
+ * wait (bounded, 10 s) for jobs on the GPU, free everything. */
+GFP_API gfp_status gfp_server_destroy(gfp_server *srv);
+/* Register a resident rows x cols matrix: `dev` (caller-owned device memory,
+ * row-major, leading dimension cols) or, when dev is NULL, generated into
+ * server memory outside the job budget from (p, seed, stream 0).  *handle
+ * identifies it in MATVEC and BLOCK jobs. */
+GFP_API gfp_status gfp_register_matrix(gfp_server *srv, uint32_t p, uint64_t rows, uint64_t cols,
+                                       const uint32_t *dev, uint64_t seed, uint64_t *handle);
+/* Queue a job; never blocks.  GFP_ERR_INVALID for malformed jobs (unknown
+ * kind or matrix, p mismatch, zero sizes), GFP_ERR_NOMEM if the job alone
+ * exceeds the budget, GFP_ERR_AGAIN if the queue is full. */
+GFP_API gfp_status gfp_submit(gfp_server *srv, const gfp_job *job, uint64_t *ticket);
+/* Non-blocking: GFP_PENDING while queued or running; otherwise fills *res and
+ * returns GFP_OK (the job's own status is res->status). */
+GFP_API gfp_status gfp_poll(gfp_server *srv, uint64_t ticket, gfp_result *res);
+/* Blocking poll with a bound: GFP_ERR_TIMEOUT if not done within timeout_us. */
+GFP_API gfp_status gfp_wait(gfp_server *srv, uint64_t ticket, uint64_t timeout_us, gfp_result *res);
+/* Copy a finished MATVEC / BLOCK job's outputs (count residues) to host memory. */
+GFP_API gfp_status gfp_result_copy(gfp_server *srv, uint64_t ticket, uint32_t *host, uint64_t count);
+/* Forget a finished job and free its outputs; cancel it if still queued. */
+GFP_API gfp_status gfp_release(gfp_server *srv, uint64_t ticket);
+GFP_API gfp_status gfp_server_get_stats(gfp_server *srv, gfp_server_stats *out);
+
 /* ---- synthetic inputs (device generator) ---- */
 
 /* out[i] = word(seed, stream_id, offset + i) mod p for 0 <= i < n, where

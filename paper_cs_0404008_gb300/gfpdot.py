@@ -58,6 +58,35 @@ class gfp_dot_desc(ctypes.Structure):
     _fields_ = [("p", _u32), ("repr", _u32), ("n", _u64), ("x", _vp), ("y", _vp)]
 
 
+class gfp_server_cfg(ctypes.Structure):
+    _fields_ = [("device", _int), ("mem_budget", _u64), ("max_inflight", _u32),
+                ("n_streams", _u32), ("queue_capacity", _u32), ("batch_window_us", _u32),
+                ("simulate", _u32), ("fail_every", _u32)]
+
+
+class gfp_job(ctypes.Structure):
+    _fields_ = [("kind", _u32), ("p", _u32), ("n", _u64), ("nb", _u64), ("matrix", _u64),
+                ("x", _vp), ("y", _vp), ("v", _vp), ("seed", _u64)]
+
+
+class gfp_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("kind", _u32), ("value", _u32), ("batch", _u32),
+                ("out_elems", _u64), ("t_submit_ns", _u64), ("t_admit_ns", _u64),
+                ("t_start_ns", _u64), ("t_done_ns", _u64)]
+
+
+class gfp_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", _u64), ("admitted", _u64), ("completed", _u64), ("failed", _u64),
+                ("cancelled", _u64), ("admission_stalls", _u64), ("dot_launches", _u64),
+                ("mem_in_use", _u64), ("mem_peak", _u64), ("mem_budget", _u64),
+                ("kernel_launches", _u64)]
+
+
+GFP_JOB_DOT = 0
+GFP_JOB_MATVEC = 1
+GFP_JOB_BLOCK = 2
+
+
 _SIGS = {
     "gfp_status_string": (ctypes.c_char_p, [_int]),
     "gfp_last_cuda_error": (ctypes.c_char_p, []),
@@ -90,6 +119,15 @@ _SIGS = {
     "gfp_plan_save": (_int, [_vp, ctypes.c_char_p]),
     "gfp_plan_size": (_u64, [_vp]),
     "gfp_fill_uniform": (_int, [_u32, _u64, _u64, _u64, _u64, _vp, _vp]),
+    "gfp_server_create": (_int, [ctypes.POINTER(gfp_server_cfg), ctypes.POINTER(_vp)]),
+    "gfp_server_destroy": (_int, [_vp]),
+    "gfp_register_matrix": (_int, [_vp, _u32, _u64, _u64, _vp, _u64, ctypes.POINTER(_u64)]),
+    "gfp_submit": (_int, [_vp, ctypes.POINTER(gfp_job), ctypes.POINTER(_u64)]),
+    "gfp_poll": (_int, [_vp, _u64, ctypes.POINTER(gfp_result)]),
+    "gfp_wait": (_int, [_vp, _u64, _u64, ctypes.POINTER(gfp_result)]),
+    "gfp_result_copy": (_int, [_vp, _u64, _vp, _u64]),
+    "gfp_release": (_int, [_vp, _u64]),
+    "gfp_server_get_stats": (_int, [_vp, ctypes.POINTER(gfp_server_stats)]),
 }
 
 _lib = None
@@ -445,3 +483,84 @@ def gfp_fill_uniform(p: int, seed: int, stream_id: int, out, n: int | None = Non
     _check(load().gfp_fill_uniform(p, seed, stream_id, offset, n, _ptr(out), _stream(stream)),
            "gfp_fill_uniform")
     return out
+
+
+# ---- service ----
+
+class Server:
+    """gfp_server: continuous batching of dot / matvec / block jobs."""
+
+    def __init__(self, device: int = 0, mem_budget: int = 0, max_inflight: int = 0,
+                 n_streams: int = 0, queue_capacity: int = 0, batch_window_us: int = 0,
+                 simulate: bool = False, fail_every: int = 0):
+        if not simulate:
+            import torch
+            torch.cuda.init()
+        cfg = gfp_server_cfg(device, mem_budget, max_inflight, n_streams, queue_capacity,
+                             batch_window_us, int(bool(simulate)), fail_every)
+        h = _vp()
+        _check(load().gfp_server_create(ctypes.byref(cfg), ctypes.byref(h)), "gfp_server_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            _check(load().gfp_server_destroy(self.handle), "gfp_server_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def register_matrix(self, p: int, rows: int, cols: int, dev=None, seed: int = 0) -> int:
+        h = _u64()
+        _check(load().gfp_register_matrix(self.handle, p, rows, cols, _ptr(dev), seed,
+                                          ctypes.byref(h)), "gfp_register_matrix")
+        return int(h.value)
+
+    def submit_status(self, kind: int, p: int, n: int = 0, nb: int = 0, matrix: int = 0,
+                      x=None, y=None, v=None, seed: int = 0):
+        """Returns (status, ticket) without raising."""
+        j = gfp_job(kind, p, n, nb, matrix, _ptr(x), _ptr(y), _ptr(v), seed)
+        t = _u64()
+        st = load().gfp_submit(self.handle, ctypes.byref(j), ctypes.byref(t))
+        return st, int(t.value)
+
+    def submit(self, *a, **k) -> int:
+        st, t = self.submit_status(*a, **k)
+        _check(st, "gfp_submit")
+        return t
+
+    def poll(self, ticket: int):
+        r = gfp_result()
+        st = load().gfp_poll(self.handle, ticket, ctypes.byref(r))
+        return st, r
+
+    def wait(self, ticket: int, timeout_us: int = 60_000_000):
+        r = gfp_result()
+        st = load().gfp_wait(self.handle, ticket, timeout_us, ctypes.byref(r))
+        return st, r
+
+    def result_copy(self, ticket: int, count: int):
+        import numpy as np
+        out = np.zeros(count, dtype=np.uint32)
+        _check(load().gfp_result_copy(self.handle, ticket, out.ctypes.data, count),
+               "gfp_result_copy")
+        return out
+
+    def release(self, ticket: int) -> int:
+        return int(load().gfp_release(self.handle, ticket))
+
+    def stats(self) -> dict:
+        s = gfp_server_stats()
+        _check(load().gfp_server_get_stats(self.handle, ctypes.byref(s)), "gfp_server_get_stats")
+        return {f: getattr(s, f) for f, _ in gfp_server_stats._fields_}
+
+
+def gfp_server_create(**kw) -> Server:
+    return Server(**kw)
+
+
+def gfp_server_destroy(srv: Server):
+    srv.close()
