@@ -59,6 +59,22 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def rank_seed(rank: int) -> int:
+    """Weak scaling: every rank runs its own batch of the same recipe."""
+    return SEED + 1000 * rank
+
+
+def reduce_max(value: float, device: str = "cpu") -> float:
+    """Max over the ranks of the default process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 # clocks sampler (nvidia-smi during the timed region)
 # ---------------------------------------------------------------------------
@@ -243,12 +259,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, "cuda")
 
     # --- autotune (install-time selection, per (p, n) bucket) ---
     t_tune = time.perf_counter()
@@ -257,7 +268,7 @@ def run_gpu(args):
     t_tune = time.perf_counter() - t_tune
 
     count = args.pairs
-    batch = Batch(g, torch, SEED + 1000 * rank, count)
+    batch = Batch(g, torch, rank_seed(rank), count)
     out = torch.empty(count, dtype=torch.int32, device="cuda")
     plan = g.BatchPlan(ctx, batch.pairs())
     n_units, _ = plan.info()
@@ -479,7 +490,7 @@ def run_secondary(args):
         })
         plan.close()
     elif args.workload == "matvec":
-        p, n, iters = 2147483647, 32768, 64
+        p, n, iters = 2147483647, args.mv_n, args.mv_iters
         A = torch.empty((n, n), dtype=torch.int32, device="cuda")
         g.gfp_fill_uniform(p, gi.BASE_SEED + 2, 0, A)
         x0 = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -506,8 +517,8 @@ def run_secondary(args):
         achieved = 4 * macs / (t / 1e3) / 1e9
         line.update({
             "value": macs / (t / 1e3) / 1e9, "ms_per_step": t,
-            "config": {"workload": "Wiedemann iteration over GF(2147483647): A 32768x32768 uint32 "
-                                   "uniform, x_{t+1} = A x_t for 64 iterations in one CUDA graph",
+            "config": {"workload": f"Wiedemann iteration over GF(2147483647): A {n}x{n} uint32 "
+                                   f"uniform, x_(t+1) = A x_t for {iters} iterations in one CUDA graph",
                        "l2": "A is 4 GiB, larger than L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "kernel": "k_matvec",
@@ -777,6 +788,8 @@ def main():
     ap.add_argument("--requests", type=int, default=20000, help="serve: Poisson requests")
     ap.add_argument("--load", type=float, default=0.7, help="serve: arrival rate / capacity")
     ap.add_argument("--block-m", type=int, default=16384, help="block workload rows (profiling)")
+    ap.add_argument("--mv-n", type=int, default=32768, help="matvec side (profiling)")
+    ap.add_argument("--mv-iters", type=int, default=64, help="matvec iterations (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -1,0 +1,60 @@
+"""Full-size workloads against the oracle: the 4096-pair batched dot workload
+(every result), and the 32768 x 32768 Wiedemann iteration over GF(2^31-1)
+(first iteration row by row, every iteration by Freivalds' check, sampled rows
+of every iteration)."""
+import numpy as np
+import pytest
+import torch
+
+import gfp_inputs as gi
+import oracle
+from gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+def test_batched_workload_full(lib, ctx):
+    seed = gi.BASE_SEED + 1
+    lens, ps = gi.batched_shapes(4096, seed)
+    off, total, x, y = gi.batched_operands(lens, ps, seed)
+    want = oracle.dot_batch(ps, lens, off, x, y)
+    xd, yd = dev(x), dev(y)
+    for repr_, mask in ((0, None), (lib.GFP_REPR_U64_CARRY, None), (lib.GFP_REPR_PERTERM, None),
+                        (lib.GFP_REPR_FP64, ps < (1 << 26))):
+        sel = np.arange(len(lens)) if mask is None else np.nonzero(mask)[0]
+        pairs = [(int(ps[i]), xd[int(off[i]):int(off[i]) + int(lens[i])],
+                  yd[int(off[i]):int(off[i]) + int(lens[i])], int(lens[i]), repr_) for i in sel]
+        plan = lib.BatchPlan(ctx, pairs)
+        out = torch.full((len(sel),), -1, dtype=torch.int32, device="cuda")
+        for _ in range(2):
+            plan.exec(out)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(out), want[sel]), repr_
+        plan.close()
+
+
+def test_wiedemann_iteration_full(lib, ctx):
+    p, n, iters = 2147483647, 32768, 64
+    seed = gi.BASE_SEED + 2
+    A = gi.uniform(p, n * n, seed, 0).reshape(n, n)
+    x0 = gi.uniform(p, n, seed, 1)
+    Ad = dev(A.ravel()).view(n, n)
+    Y = torch.full((iters * n,), -1, dtype=torch.int32, device="cuda")
+    lib.gfp_matvec_iterate(ctx, p, Ad, dev(x0), Y, iters)
+    torch.cuda.synchronize()
+    Yh = host(Y).reshape(iters, n)
+    del Ad
+    # iteration 1, every row
+    assert np.array_equal(Yh[0], oracle.matvec(p, A, x0))
+    # Freivalds per iteration: u^T (A y_{t-1}) = (u^T A) y_{t-1}, w = A^T u from the oracle
+    u = gi.uniform(p, n, seed, 2)
+    w = oracle.matvec(p, np.ascontiguousarray(A.T), u)
+    prev = x0
+    rows = gi.words(seed, 3, 64) % np.uint64(n)
+    for t in range(iters):
+        assert oracle.dot(p, u, Yh[t]) == oracle.dot(p, w, prev), t
+        # sampled rows: y_t[i] = A_i . y_{t-1}
+        for i in rows[:8]:
+            i = int(i)
+            assert int(Yh[t][i]) == oracle.dot(p, A[i], prev), (t, i)
+        prev = Yh[t]
