@@ -44,19 +44,24 @@ constexpr int BK = 64;             // K per k-block: one 128-byte swizzle row of
 constexpr int NT = 64;             // output columns per n-tile
 constexpr int MMA_N = 2 * NT;      // hi and lo digits of B stacked along N
 constexpr int KC = 16;             // k-blocks per exact chunk (1024 terms)
-#ifndef GFP_BLK_KB_PER_BOX
-#define GFP_BLK_KB_PER_BOX 1
+#ifndef GFP_BLK_SLOTS
+#define GFP_BLK_SLOTS 3
 #endif
-#ifndef GFP_BLK_SA
-#define GFP_BLK_SA 3
+#ifndef GFP_BLK_BSTAGES
+#define GFP_BLK_BSTAGES 2
 #endif
-constexpr int KBB = GFP_BLK_KB_PER_BOX;   // k-blocks per A box (longer row bursts for HBM)
-constexpr int SA = GFP_BLK_SA;            // A staging slots (uint32 boxes landed by TMA)
-constexpr int STAGES = 2;                 // digit stages (A hi, A lo, B) consumed by the MMAs
-constexpr int A_TILE_BYTES = BM * BK * 4 * KBB;               // 32 KiB of uint32 per k-block
-constexpr int A_DIGIT_BYTES = BM * BK * 2;                    // 16 KiB
+#ifndef GFP_BLK_KBB
+#define GFP_BLK_KBB 2
+#endif
+constexpr int KBB = GFP_BLK_KBB;          // k-blocks per A slot (longer row bursts per TMA box)
+constexpr int SLOTS = GFP_BLK_SLOTS;      // A slots: a uint32 box lands (TMA), is converted in
+                                          // place into fp16 digit tiles, then read by the MMAs
+constexpr int BSTAGES = GFP_BLK_BSTAGES;  // B digit tiles in flight (own ring, off the A path)
+constexpr int A_TILE_BYTES = BM * BK * 4;                     // 32 KiB of uint32 per k-block
+constexpr int SLOT_BYTES = KBB * A_TILE_BYTES;
+constexpr int A_DIGIT_BYTES = BM * BK * 2;                    // 16 KiB per digit
 constexpr int B_TILE_BYTES = MMA_N * BK * 2;                  // 16 KiB
-constexpr int STAGE_BYTES = 2 * A_DIGIT_BYTES + B_TILE_BYTES; // 48 KiB
+static_assert(A_TILE_BYTES == 2 * A_DIGIT_BYTES, "in-place conversion needs equal sizes");
 constexpr int CONV_WARPS = 8;
 constexpr int EPI_WARPS = 4;
 constexpr int W_APROD = 0, W_MMA = 1, W_BPROD = 2, W_CONV0 = 3, W_EPI0 = W_CONV0 + CONV_WARPS;
@@ -66,11 +71,11 @@ constexpr uint64_t WAIT_NS = 2000000000ull;   // bounded waits: 2 s
 constexpr uint32_t IDESC = ptx::idesc_f16_f32(BM, MMA_N);
 
 struct Bars {
-    uint64_t a_full[SA];       // uint32 A tile landed (1 arrival + tx bytes)
-    uint64_t a_empty[SA];      // A tile read by the converters (one arrival per converter warp)
-    uint64_t full_b[STAGES];   // B digit tile landed (1 arrival + tx bytes)
-    uint64_t full_a[STAGES];   // A digit tiles written (one arrival per converter warp)
-    uint64_t empty[STAGES];    // MMAs reading the stage completed (tcgen05.commit)
+    uint64_t a_full[SLOTS];    // uint32 A tile landed (1 arrival + tx bytes)
+    uint64_t conv[SLOTS];      // digits written in place (one arrival per converter warp)
+    uint64_t a_empty[SLOTS];   // MMAs reading the digits completed (tcgen05.commit)
+    uint64_t full_b[BSTAGES];  // B digit tile landed (1 arrival + tx bytes)
+    uint64_t empty_b[BSTAGES]; // MMAs reading the B tile completed (tcgen05.commit)
     uint64_t acc_full[2];      // accumulator set ready (tcgen05.commit)
     uint64_t acc_empty[2];     // accumulator set drained (one arrival per epilogue warp)
     uint64_t drain;            // all MMAs issued by this CTA completed
@@ -78,8 +83,8 @@ struct Bars {
     uint32_t abort;
     uint32_t last_flag;
 };
-constexpr size_t SMEM_BYTES =
-    1024 /*alignment slack*/ + (size_t)SA * A_TILE_BYTES + (size_t)STAGES * STAGE_BYTES + 1024;
+constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + (size_t)SLOTS * SLOT_BYTES +
+                              (size_t)BSTAGES * B_TILE_BYTES + 1024;
 static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 
 struct Args {
@@ -163,11 +168,27 @@ __device__ __forceinline__ void split_pair(uint32_t a0, uint32_t a1, uint32_t p,
     hi2 = *reinterpret_cast<const uint32_t *>(&hi);
 }
 
-// Converter thread ct (0..255): 8 chunks of 4 consecutive K of one row, read
-// from the landed uint32 tile (row-major, 256 bytes per row) and written as
-// digits into the two 128-byte-swizzled K-major fp16 tiles of a stage.
-__device__ __forceinline__ void convert_tile(const Args &a, const uint8_t *atile, uint8_t *stage,
-                                             int ct, int sub)
+// Converter thread ct (0..255) handles 8 chunks of 4 consecutive K of one row.
+// load_tile copies them from the landed uint32 tile (row-major, 256 bytes per
+// row) into registers; once every converter thread has done so, store_digits
+// overwrites the same 32 KiB with the two 128-byte-swizzled K-major fp16
+// digit tiles (high digits first).
+struct ARegs {
+    uint4 v[8];
+};
+
+// sub-tile `sub` of a slot holding KBB k-blocks (row stride BK*4*KBB bytes)
+__device__ __forceinline__ void load_tile(const uint8_t *slot, int sub, int ct, ARegs &r)
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int q = ct + 256 * i;
+        const int row = q >> 4, c4 = q & 15;
+        r.v[i] = *reinterpret_cast<const uint4 *>(slot + row * (BK * 4 * KBB) + sub * (BK * 4) + c4 * 16);
+    }
+}
+
+__device__ __forceinline__ void store_digits(const Args &a, const ARegs &r, uint8_t *stage, int ct)
 {
     uint8_t *th = stage;                    // high digits
     uint8_t *tl = stage + A_DIGIT_BYTES;    // low digits
@@ -175,11 +196,9 @@ __device__ __forceinline__ void convert_tile(const Args &a, const uint8_t *atile
     for (int i = 0; i < 8; ++i) {
         const int q = ct + 256 * i;
         const int row = q >> 4, c4 = q & 15;
-        const uint4 v =
-            *reinterpret_cast<const uint4 *>(atile + row * (BK * 4 * KBB) + sub * (BK * 4) + c4 * 16);
         uint32_t h01, l01, h23, l23;
-        split_pair(v.x, v.y, a.mod.p, a.half, h01, l01);
-        split_pair(v.z, v.w, a.mod.p, a.half, h23, l23);
+        split_pair(r.v[i].x, r.v[i].y, a.mod.p, a.half, h01, l01);
+        split_pair(r.v[i].z, r.v[i].w, a.mod.p, a.half, h23, l23);
         // 128-byte swizzle: 16-byte chunk j of row r sits at chunk j ^ (r & 7)
         const int j = c4 >> 1, halfsel = c4 & 1;
         const uint32_t off = (uint32_t)row * 128u + ((uint32_t)(j ^ (row & 7)) << 4) + (halfsel << 3);
@@ -192,23 +211,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *stg = smem;                                      // SA uint32 A tiles
-    uint8_t *dig = smem + (size_t)SA * A_TILE_BYTES;          // STAGES digit stages
-    Bars *bars = reinterpret_cast<Bars *>(dig + (size_t)STAGES * STAGE_BYTES);
+    uint8_t *slot_mem = smem;                                  // SLOTS A slots
+    uint8_t *bst = smem + (size_t)SLOTS * SLOT_BYTES;          // BSTAGES B digit tiles
+    Bars *bars = reinterpret_cast<Bars *>(bst + (size_t)BSTAGES * B_TILE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const uint64_t u0 = a.units * blockIdx.x / gridDim.x;
     const uint64_t u1 = a.units * (blockIdx.x + 1) / gridDim.x;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < SA; ++s) {
+        for (int s = 0; s < SLOTS; ++s) {
             ptx::mbar_init(ptx::smem_u32(&bars->a_full[s]), 1);
-            ptx::mbar_init(ptx::smem_u32(&bars->a_empty[s]), CONV_WARPS);
+            ptx::mbar_init(ptx::smem_u32(&bars->conv[s]), CONV_WARPS);
+            ptx::mbar_init(ptx::smem_u32(&bars->a_empty[s]), 1);
         }
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < BSTAGES; ++s) {
             ptx::mbar_init(ptx::smem_u32(&bars->full_b[s]), 1);
-            ptx::mbar_init(ptx::smem_u32(&bars->full_a[s]), CONV_WARPS);
-            ptx::mbar_init(ptx::smem_u32(&bars->empty[s]), 1);
+            ptx::mbar_init(ptx::smem_u32(&bars->empty_b[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(ptx::smem_u32(&bars->acc_full[b]), 1);
@@ -230,31 +249,31 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
     volatile uint32_t *abort = &bars->abort;
 
     if (warp == W_APROD) {
-        // ---------------- producer: uint32 A boxes (TMA, KBB k-blocks each) ----------------
+        // ---------------- producer: uint32 A tiles (TMA) into free slots ----------------
         if (lane == 0) {
-            int armed[SA];
-            for (int s = 0; s < SA; ++s) armed[s] = -1;
-            uint32_t bi = 0;
+            int armed[SLOTS];
+            for (int s = 0; s < SLOTS; ++s) armed[s] = -1;
+            uint32_t si = 0;   // slot sequence number
             bool ok = true;
             ptx::prefetch_tensormap(&a.tmap_a);
             for (uint64_t u = u0; u < u1 && ok; ++u) {
                 const UnitPos q = unit_pos(a, u);
-                for (uint32_t kb = q.kb0; kb < q.kb1; kb += KBB, ++bi) {
-                    const uint32_t s = bi % SA, round = bi / SA;
+                for (uint32_t kb = q.kb0; kb < q.kb1; kb += KBB, ++si) {
+                    const uint32_t s = si % SLOTS, round = si / SLOTS;
                     if (round > 0 &&
                         !wait_bar(ptx::smem_u32(&bars->a_empty[s]), (round - 1) & 1, abort, a.err)) {
                         ok = false;
                         break;
                     }
                     const uint32_t fb = ptx::smem_u32(&bars->a_full[s]);
-                    ptx::mbar_arrive_expect_tx(fb, A_TILE_BYTES);
-                    ptx::tma_load_2d(ptx::smem_u32(stg + (size_t)s * A_TILE_BYTES), &a.tmap_a,
+                    ptx::mbar_arrive_expect_tx(fb, SLOT_BYTES);
+                    ptx::tma_load_2d(ptx::smem_u32(slot_mem + (size_t)s * SLOT_BYTES), &a.tmap_a,
                                      (int)(kb * BK), (int)(q.mt * BM), fb);
                     armed[s] = (int)round;
                 }
             }
             // copies already issued must land before the CTA can exit
-            for (int s = 0; s < SA; ++s) {
+            for (int s = 0; s < SLOTS; ++s) {
                 if (armed[s] < 0) continue;
                 const uint32_t fb = ptx::smem_u32(&bars->a_full[s]);
                 const uint64_t t0 = ptx::globaltimer();
@@ -265,28 +284,28 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
     } else if (warp == W_BPROD) {
         // ---------------- producer: B digit tiles (bulk copies from the prepared image) ----------------
         if (lane == 0) {
-            int armed[STAGES];
-            for (int s = 0; s < STAGES; ++s) armed[s] = -1;
+            int armed[BSTAGES];
+            for (int s = 0; s < BSTAGES; ++s) armed[s] = -1;
             uint32_t it = 0;
             bool ok = true;
             for (uint64_t u = u0; u < u1 && ok; ++u) {
                 const UnitPos q = unit_pos(a, u);
                 for (uint32_t kb = q.kb0; kb < q.kb1; ++kb, ++it) {
-                    const uint32_t s = it % STAGES, round = it / STAGES;
+                    const uint32_t s = it % BSTAGES, round = it / BSTAGES;
                     if (round > 0 &&
-                        !wait_bar(ptx::smem_u32(&bars->empty[s]), (round - 1) & 1, abort, a.err)) {
+                        !wait_bar(ptx::smem_u32(&bars->empty_b[s]), (round - 1) & 1, abort, a.err)) {
                         ok = false;
                         break;
                     }
                     const uint32_t fb = ptx::smem_u32(&bars->full_b[s]);
                     ptx::mbar_arrive_expect_tx(fb, B_TILE_BYTES);
-                    ptx::bulk_g2s(ptx::smem_u32(dig + (size_t)s * STAGE_BYTES + 2 * A_DIGIT_BYTES),
+                    ptx::bulk_g2s(ptx::smem_u32(bst + (size_t)s * B_TILE_BYTES),
                                   a.Bimg + ((uint64_t)q.nt * a.kblocks + kb) * B_TILE_BYTES,
                                   B_TILE_BYTES, fb);
                     armed[s] = (int)round;
                 }
             }
-            for (int s = 0; s < STAGES; ++s) {
+            for (int s = 0; s < BSTAGES; ++s) {
                 if (armed[s] < 0) continue;
                 const uint32_t fb = ptx::smem_u32(&bars->full_b[s]);
                 const uint64_t t0 = ptx::globaltimer();
@@ -297,7 +316,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
     } else if (warp == W_MMA) {
         // ---------------- MMA issue (one thread) ----------------
         if (lane == 0) {
-            uint32_t it = 0;
+            uint32_t it = 0, si = 0;
             bool ok = true;
             uint64_t idx = 0;
             for (uint64_t u = u0; u < u1 && ok; ++u, ++idx) {
@@ -312,17 +331,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                 const uint32_t d_hi = tmem + b * 256u;         // A high digit x [B hi | B lo]
                 const uint32_t d_lo = tmem + b * 256u + 128u;  // A low digit  x [B hi | B lo]
                 for (uint32_t kb = q.kb0; kb < q.kb1; ++kb, ++it) {
-                    const uint32_t s = it % STAGES, round = it / STAGES;
-                    if (!wait_bar(ptx::smem_u32(&bars->full_b[s]), round & 1, abort, a.err) ||
-                        !wait_bar(ptx::smem_u32(&bars->full_a[s]), round & 1, abort, a.err)) {
+                    const uint32_t sub = (kb - q.kb0) % KBB;
+                    const uint32_t s = si % SLOTS, round = si / SLOTS;
+                    const uint32_t sb = it % BSTAGES, roundb = it / BSTAGES;
+                    if (!wait_bar(ptx::smem_u32(&bars->full_b[sb]), roundb & 1, abort, a.err) ||
+                        (sub == 0 && !wait_bar(ptx::smem_u32(&bars->conv[s]), round & 1, abort, a.err))) {
                         ok = false;
                         break;
                     }
                     ptx::tc_fence_after();
-                    const uint32_t base = ptx::smem_u32(dig + (size_t)s * STAGE_BYTES);
+                    const uint32_t base =
+                        ptx::smem_u32(slot_mem + (size_t)s * SLOT_BYTES + (size_t)sub * A_TILE_BYTES);
                     const uint64_t dah = ptx::sdesc_k_sw128(base);
                     const uint64_t dal = ptx::sdesc_k_sw128(base + A_DIGIT_BYTES);
-                    const uint64_t db = ptx::sdesc_k_sw128(base + 2 * A_DIGIT_BYTES);
+                    const uint64_t db = ptx::sdesc_k_sw128(ptx::smem_u32(bst + (size_t)sb * B_TILE_BYTES));
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint32_t acc = (kb > q.kb0 || kk > 0) ? 1u : 0u;
@@ -330,7 +352,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                         ptx::mma_f16(d_hi, dah + 2 * kk, db + 2 * kk, IDESC, acc);
                         ptx::mma_f16(d_lo, dal + 2 * kk, db + 2 * kk, IDESC, acc);
                     }
-                    ptx::mma_commit(ptx::smem_u32(&bars->empty[s]));
+                    ptx::mma_commit(ptx::smem_u32(&bars->empty_b[sb]));
+                    if (sub == KBB - 1 || kb + 1 == q.kb1) {   // last k-block of this slot
+                        ptx::mma_commit(ptx::smem_u32(&bars->a_empty[s]));
+                        ++si;
+                    }
                 }
                 if (!ok) break;
                 ptx::mma_commit(ptx::smem_u32(&bars->acc_full[b]));
@@ -343,35 +369,35 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
             }
         }
     } else if (warp < W_EPI0) {
-        // ---------------- converters: uint32 tile -> centred fp16 digits ----------------
+        // ---------------- converters: uint32 tiles -> centred fp16 digits, in place ----------------
         const int ct = threadIdx.x - 32 * W_CONV0;   // 0..255
-        uint32_t it = 0, bi = 0;
-        bool ok = true;
-        for (uint64_t u = u0; u < u1 && ok; ++u) {
+        uint32_t si = 0;
+        for (uint64_t u = u0; u < u1; ++u) {
             const UnitPos q = unit_pos(a, u);
-            for (uint32_t kb = q.kb0; kb < q.kb1 && ok; kb += KBB, ++bi) {
-                const uint32_t sa = bi % SA, ra = bi / SA;
-                if (!warp_wait(ptx::smem_u32(&bars->a_full[sa]), ra & 1, abort, a.err)) {
+            bool ok = true;
+            for (uint32_t kb = q.kb0; kb < q.kb1; kb += KBB, ++si) {
+                const uint32_t s = si % SLOTS, round = si / SLOTS;
+                const bool got = warp_wait(ptx::smem_u32(&bars->a_full[s]), round & 1, abort, a.err);
+                // all converter warps read the box before any overwrites it; decide together
+                if (ptx::bar_red_or<2, CONV_WARPS * 32>(!got || *abort != 0)) {
                     ok = false;
                     break;
                 }
+                uint8_t *slot = slot_mem + (size_t)s * SLOT_BYTES;
                 const uint32_t nsub = min((uint32_t)KBB, q.kb1 - kb);
-                for (uint32_t sub = 0; sub < nsub; ++sub, ++it) {
-                    const uint32_t s = it % STAGES, round = it / STAGES;
-                    if (round > 0 &&
-                        !warp_wait(ptx::smem_u32(&bars->empty[s]), (round - 1) & 1, abort, a.err)) {
-                        ok = false;
-                        break;
-                    }
-                    convert_tile(a, stg + (size_t)sa * A_TILE_BYTES, dig + (size_t)s * STAGE_BYTES, ct,
-                                 (int)sub);
-                    ptx::fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&bars->full_a[s]));
-                }
-                if (!ok) break;
-                if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&bars->a_empty[sa]));
+                ARegs r[KBB];
+#pragma unroll
+                for (int sub = 0; sub < KBB; ++sub)
+                    if ((uint32_t)sub < nsub) load_tile(slot, sub, ct, r[sub]);
+                asm volatile("bar.sync 2, %0;" ::"n"(CONV_WARPS * 32) : "memory");
+#pragma unroll
+                for (int sub = 0; sub < KBB; ++sub)
+                    if ((uint32_t)sub < nsub) store_digits(a, r[sub], slot + (size_t)sub * A_TILE_BYTES, ct);
+                ptx::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&bars->conv[s]));
             }
+            if (!ok) break;
         }
     } else {
         // ---------------- epilogue: TMEM -> residues ----------------
@@ -440,12 +466,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                 }
                 asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32));
                 if (bars->last_flag) {
+                    // every contribution to this tile is in L2 (atomics, then fences, then
+                    // the ticket): read the row with L2 loads issued together, reduce,
+                    // write C and clear the partial sums for the next call
                     if (grow < a.m) {
-                        for (int j = 0; j < NT; ++j) {
-                            if (col0 + j >= a.nb) break;
-                            uint32_t *cell = &a.Cacc[grow * ldacc + col0 + j];
-                            const uint32_t v = atomicExch(cell, 0u);
-                            a.C[grow * a.ldc + col0 + j] = reduce64(v, a.mod);
+                        uint32_t *row = &a.Cacc[grow * ldacc + col0];   // 16-byte aligned
+                        uint4 v[NT / 4];
+#pragma unroll
+                        for (int q4 = 0; q4 < NT / 4; ++q4) v[q4] = __ldcg(reinterpret_cast<const uint4 *>(row) + q4);
+#pragma unroll
+                        for (int q4 = 0; q4 < NT / 4; ++q4)
+                            __stcg(reinterpret_cast<uint4 *>(row) + q4, make_uint4(0u, 0u, 0u, 0u));
+                        uint32_t *crow = a.C + grow * a.ldc + col0;
+#pragma unroll
+                        for (int q4 = 0; q4 < NT / 4; ++q4) {
+                            const uint32_t w[4] = {v[q4].x, v[q4].y, v[q4].z, v[q4].w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (col0 + 4 * q4 + e < a.nb) crow[4 * q4 + e] = reduce64(w[e], a.mod);
                         }
                     }
                     asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32));
