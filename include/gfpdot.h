@@ -264,6 +264,15 @@ GFP_API gfp_status gfp_matmul_block_csr(gfp_ctx *ctx, uint32_t p, uint64_t m, ui
  * CUDA error is pending (GFP_ERR_CUDA).  GFP_OK otherwise. */
 GFP_API gfp_status gfp_context_check(gfp_ctx *ctx);
 
+/* Failure-detection self test (no counterpart in the paper): launches one
+ * thread that waits, with the same bounded wait the tensor-core kernel uses
+ * for its pipeline barriers, on a barrier nothing arrives on.  The wait must
+ * give up after limit_ns (1 ms <= limit_ns <= 2 s) and report it: the call
+ * synchronises `stream` and returns GFP_ERR_TIMEOUT when the expiry was
+ * detected (the expected outcome; the context stays usable), GFP_OK if the
+ * wait somehow completed, GFP_ERR_INVALID for a limit out of range. */
+GFP_API gfp_status gfp_wait_selftest(uint64_t limit_ns, void *stream);
+
 /* ---- install-time tuning (automated empirical optimisation, Section 4) ---- */
 
 /* Time every eligible representation (U64_BLOCK, U64_CARRY, FP64) and

@@ -103,8 +103,11 @@ struct Args {
     uint64_t units;
 };
 
+// Bounded wait on an mbarrier phase: gives up after limit_ns (or as soon as
+// another role of the CTA has given up), sets the CTA abort flag and bit 0 of
+// the error word, and returns false.
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile uint32_t *abort,
-                                         uint32_t *err)
+                                         uint32_t *err, uint64_t limit_ns = WAIT_NS)
 {
     uint64_t t0 = 0;
     for (uint32_t i = 0;; ++i) {
@@ -113,7 +116,7 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile
             if (*abort) return false;
             const uint64_t t = ptx::globaltimer();
             if (t0 == 0) t0 = t;
-            else if (t - t0 > WAIT_NS) {
+            else if (t - t0 > limit_ns) {
                 *abort = 1u;
                 atomicOr(err, 1u);
                 return false;
@@ -121,6 +124,25 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile
         }
     }
 }
+
+// Failure-detection self test: one thread waits on an mbarrier that nothing
+// arrives on; the bounded wait must expire and report it in *err.
+__global__ void k_wait_selftest(uint64_t limit_ns, uint32_t *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t abort;
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(ptx::smem_u32(&bar), 1);
+        abort = 0;
+        ptx::fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!wait_bar(ptx::smem_u32(&bar), 0, &abort, err, limit_ns)) atomicOr(err, 2u);
+    }
+}
+
+__device__ uint32_t g_selftest_err;
 
 // warp-uniform bounded wait: lane 0 polls, the result is broadcast
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile uint32_t *abort,
@@ -717,6 +739,22 @@ static cudaError_t cc_launch(const Mod &mod, uint64_t kb, uint64_t m, uint64_t k
     dim3 grid((unsigned)((nb + CC_TN - 1) / CC_TN), (unsigned)((m + CC_TM - 1) / CC_TM));
     k_block_cc<Acc><<<grid, CC_THREADS, 0, s>>>(mod, kb, m, k, nb, A, lda, B, ldb, C, ldc);
     return cudaGetLastError();
+}
+
+cudaError_t wait_selftest(uint64_t limit_ns, cudaStream_t s, uint32_t *status_bits)
+{
+    uint32_t zero = 0;
+    cudaError_t e = cudaMemcpyToSymbolAsync(blk::g_selftest_err, &zero, 4, 0, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    uint32_t *dptr = nullptr;
+    e = cudaGetSymbolAddress((void **)&dptr, blk::g_selftest_err);
+    if (e != cudaSuccess) return e;
+    blk::k_wait_selftest<<<1, 32, 0, s>>>(limit_ns, dptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyFromSymbolAsync(status_bits, blk::g_selftest_err, 4, 0, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
 }
 
 cudaError_t launch_block_cc(Repr r, const Mod &mod, uint64_t kbound, uint64_t m, uint64_t k,

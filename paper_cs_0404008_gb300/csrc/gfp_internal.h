@@ -81,6 +81,8 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
                             uint64_t lda, const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc,
                             void *ws, int sm_count, cudaStream_t s, int *launches);
 uint32_t *block_tc_err_flag(void *ws, uint64_t m, uint64_t k, uint64_t nb);
+// Runs the bounded-wait self test; *status_bits gets the device error word.
+cudaError_t wait_selftest(uint64_t limit_ns, cudaStream_t s, uint32_t *status_bits);
 cudaError_t launch_block_cc(Repr r, const Mod &mod, uint64_t kbound, uint64_t m, uint64_t k,
                             uint64_t nb, const uint32_t *A, uint64_t lda, const uint32_t *B,
                             uint64_t ldb, uint32_t *C, uint64_t ldc, cudaStream_t s);
@@ -122,7 +124,11 @@ struct gfp_ctx {
     void *bw = nullptr;
     size_t bw_bytes = 0;
     size_t bw_slots_off = (size_t)-1;   // offset of the scratch region last cleared
-    // host-buffer staging for gfp_dot_batched_host
+    // host-buffer staging for gfp_dot_batched_host; copies are split over
+    // several streams so that more than one copy engine moves them
+    static constexpr int kCopyStreams = 4;
+    cudaStream_t copy_streams[kCopyStreams] = {};
+    cudaEvent_t copy_events[kCopyStreams + 1] = {};
     uint32_t *stage = nullptr;
     size_t stage_elems = 0;
     uint32_t *stage_out = nullptr;

@@ -398,6 +398,10 @@ GFP_API gfp_status gfp_context_destroy(gfp_ctx *ctx)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    for (int i = 0; i < gfp_ctx::kCopyStreams; ++i)
+        if (ctx->copy_streams[i]) cudaStreamDestroy(ctx->copy_streams[i]);
+    for (int i = 0; i <= gfp_ctx::kCopyStreams; ++i)
+        if (ctx->copy_events[i]) cudaEventDestroy(ctx->copy_events[i]);
     cudaFree(ctx->ring_slots);
     if (ctx->bw) cudaFree(ctx->bw);
     if (ctx->stage) cudaFree(ctx->stage);
@@ -595,8 +599,26 @@ GFP_API gfp_status gfp_dot_batched_host(gfp_ctx *ctx, uint64_t count, const uint
     }
     uint32_t *dx = ctx->stage, *dy = ctx->stage + (total ? total : 1);
     if (total) {
-        GFP_CUDA_TRY(cudaMemcpyAsync(dx, x_host, total * 4, cudaMemcpyHostToDevice, s));
-        GFP_CUDA_TRY(cudaMemcpyAsync(dy, y_host, total * 4, cudaMemcpyHostToDevice, s));
+        if (!ctx->copy_streams[0]) {
+            for (int i = 0; i < gfp_ctx::kCopyStreams; ++i)
+                GFP_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy_streams[i], cudaStreamNonBlocking));
+            for (int i = 0; i <= gfp_ctx::kCopyStreams; ++i)
+                GFP_CUDA_TRY(cudaEventCreateWithFlags(&ctx->copy_events[i], cudaEventDisableTiming));
+        }
+        // the copies may overwrite staging that earlier work on `s` still reads
+        GFP_CUDA_TRY(cudaEventRecord(ctx->copy_events[gfp_ctx::kCopyStreams], s));
+        const uint64_t per = (total + gfp_ctx::kCopyStreams - 1) / gfp_ctx::kCopyStreams;
+        for (int i = 0; i < gfp_ctx::kCopyStreams; ++i) {
+            const uint64_t b = (uint64_t)i * per;
+            if (b >= total) break;
+            const uint64_t len = std::min<uint64_t>(per, total - b);
+            cudaStream_t cs = ctx->copy_streams[i];
+            GFP_CUDA_TRY(cudaStreamWaitEvent(cs, ctx->copy_events[gfp_ctx::kCopyStreams], 0));
+            GFP_CUDA_TRY(cudaMemcpyAsync(dx + b, x_host + b, len * 4, cudaMemcpyHostToDevice, cs));
+            GFP_CUDA_TRY(cudaMemcpyAsync(dy + b, y_host + b, len * 4, cudaMemcpyHostToDevice, cs));
+            GFP_CUDA_TRY(cudaEventRecord(ctx->copy_events[i], cs));
+            GFP_CUDA_TRY(cudaStreamWaitEvent(s, ctx->copy_events[i], 0));
+        }
     }
     std::vector<gfp_dot_desc> d(count);
     for (uint64_t j = 0; j < count; ++j)
@@ -792,6 +814,14 @@ GFP_API gfp_status gfp_context_check(gfp_ctx *ctx)
         return GFP_ERR_TIMEOUT;
     }
     return GFP_OK;
+}
+
+GFP_API gfp_status gfp_wait_selftest(uint64_t limit_ns, void *stream)
+{
+    if (limit_ns < 1000000ull || limit_ns > 2000000000ull) return GFP_ERR_INVALID;
+    uint32_t bits = 0;
+    GFP_CUDA_TRY(wait_selftest(limit_ns, as_stream(stream), &bits));
+    return (bits & 1u) ? GFP_ERR_TIMEOUT : GFP_OK;
 }
 
 GFP_API gfp_status gfp_fill_uniform(uint32_t p, uint64_t seed, uint64_t stream_id,

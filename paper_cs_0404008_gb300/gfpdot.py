@@ -114,6 +114,7 @@ _SIGS = {
     "gfp_matmul_block_csr": (_int, [_vp, _u32, _u64, _u64, _u64, _vp, _vp, _vp, _vp, _u64, _vp, _u64,
                                     _vp]),
     "gfp_context_check": (_int, [_vp]),
+    "gfp_wait_selftest": (_int, [_u64, _vp]),
     "gfp_tune": (_int, [_vp, _vp, _u32, _u32, _u32, ctypes.c_char_p]),
     "gfp_plan_load": (_int, [_vp, ctypes.c_char_p]),
     "gfp_plan_save": (_int, [_vp, ctypes.c_char_p]),
@@ -449,6 +450,11 @@ def gfp_matmul_block_csr(ctx: Context, p: int, k: int, row_ptr, col, val, B, C, 
 def gfp_context_check(ctx: Context) -> int:
     """Synchronise; returns the status (GFP_OK, GFP_ERR_TIMEOUT, GFP_ERR_CUDA)."""
     return int(load().gfp_context_check(ctx.handle))
+
+
+def gfp_wait_selftest(limit_ns: int, stream=None) -> int:
+    """Returns the status (GFP_ERR_TIMEOUT expected: the bounded wait expired)."""
+    return int(load().gfp_wait_selftest(limit_ns, _stream(stream)))
 
 
 # ---- tuning ----

@@ -161,3 +161,18 @@ def test_csr_validation(lib, fresh):
     lib.gfp_matmul_block_csr(fresh, p, k, dev(row_ptr), dev(col), dev(val), dev2(B), C)
     torch.cuda.synchronize()
     assert np.array_equal(host(C), oracle.csr(p, row_ptr, col, val, B))
+
+
+def test_bounded_wait_expires_and_context_survives(lib, fresh):
+    """A pipeline wait that nothing satisfies gives up after its limit and
+    reports GFP_ERR_TIMEOUT; the context keeps working afterwards."""
+    import time
+    t0 = time.time()
+    assert lib.gfp_wait_selftest(50_000_000) == lib.GFP_ERR_TIMEOUT
+    assert time.time() - t0 < 5
+    assert lib.gfp_wait_selftest(10) == lib.GFP_ERR_INVALID
+    p = 65521
+    A = gi.uniform(p, 128 * 256, 80, 0).reshape(128, 256)
+    B = gi.uniform(p, 256 * 64, 80, 1).reshape(256, 64)
+    fresh.set_repr(lib.GFP_REPR_F16TC)
+    assert np.array_equal(run_block(lib, fresh, p, A, B), oracle.block(p, A, B))
