@@ -230,6 +230,20 @@ GFP_API gfp_status gfp_matvec_iterate(gfp_ctx *ctx, uint32_t p, uint64_t n, cons
                                       uint64_t lda, const uint32_t *x0, uint32_t *Y,
                                       uint32_t iters, void *stream);
 
+/* The scalar sequence of a Wiedemann-style iteration (the iterative methods
+ * the introduction names as users of the dot product): seq[t] = u^T A^t x0
+ * mod p for t = 0 .. iters, with x_{t+1} = A x_t.  Each product's projection
+ * onto u is fused into the matrix-vector kernel's epilogue (no second pass
+ * over y).  A: device n x n (lda >= n); x0, u: device, n; seq: device,
+ * iters + 1; Y: device iters x n receiving x_1 .. x_iters, or NULL to keep
+ * them in context scratch.  The launches are captured once in a CUDA graph
+ * (cached per argument set) and replayed with one graph launch; scratch is
+ * grown on the first call, so make it outside stream capture.  Calls sharing
+ * one context must not overlap on different streams.  iters <= 65535. */
+GFP_API gfp_status gfp_matvec_sequence(gfp_ctx *ctx, uint32_t p, uint64_t n, const uint32_t *A,
+                                       uint64_t lda, const uint32_t *x0, const uint32_t *u,
+                                       uint32_t iters, uint32_t *seq, uint32_t *Y, void *stream);
+
 /* ---- block products (dense contraction of many dot products) ---- */
 
 /* C[i*ldc + j] = (sum_t A[i*lda + t] * B[t*ldb + j]) mod p, 0 <= i < m,

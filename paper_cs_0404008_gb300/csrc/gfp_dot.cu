@@ -105,6 +105,11 @@ __global__ void __launch_bounds__(DOT_THREADS)
                  const uint32_t *__restrict__ y, unsigned long long *slot, uint32_t *ticket,
                  uint32_t *out)
 {
+    // Programmatic dependent launch: let the next kernel of the stream be
+    // scheduled now, and wait here until the previous one has finished and
+    // its writes are visible (it may have produced x or y).
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     Acc acc;
     acc.init(m, k);
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
@@ -223,25 +228,36 @@ int dot_single_grid(Repr r, uint64_t n, int sm_count)
     return (int)(want < cap ? want : cap);
 }
 
+template <class Acc>
+static cudaError_t launch_single_pdl(const Mod &m, uint64_t k, uint64_t n, const uint32_t *x,
+                                     const uint32_t *y, unsigned long long *slot, uint32_t *ticket,
+                                     uint32_t *out, int grid, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(DOT_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_dot_single<Acc>, m, k, n, x, y, slot, ticket, out);
+}
+
 cudaError_t launch_dot_single(Repr r, const Mod &m, uint64_t k, uint64_t n, const uint32_t *x,
                               const uint32_t *y, unsigned long long *slot, uint32_t *ticket,
                               uint32_t *out, int grid, cudaStream_t s)
 {
+    cudaError_t e;
     switch (r) {
-    case U64_BLOCK:
-        k_dot_single<AccBlock><<<grid, DOT_THREADS, 0, s>>>(m, k, n, x, y, slot, ticket, out);
-        break;
-    case U64_CARRY:
-        k_dot_single<AccCarry><<<grid, DOT_THREADS, 0, s>>>(m, k, n, x, y, slot, ticket, out);
-        break;
-    case FP64:
-        k_dot_single<AccF64><<<grid, DOT_THREADS, 0, s>>>(m, k, n, x, y, slot, ticket, out);
-        break;
-    default:
-        k_dot_single<AccPerTerm><<<grid, DOT_THREADS, 0, s>>>(m, k, n, x, y, slot, ticket, out);
-        break;
+    case U64_BLOCK: e = launch_single_pdl<AccBlock>(m, k, n, x, y, slot, ticket, out, grid, s); break;
+    case U64_CARRY: e = launch_single_pdl<AccCarry>(m, k, n, x, y, slot, ticket, out, grid, s); break;
+    case FP64: e = launch_single_pdl<AccF64>(m, k, n, x, y, slot, ticket, out, grid, s); break;
+    default: e = launch_single_pdl<AccPerTerm>(m, k, n, x, y, slot, ticket, out, grid, s); break;
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 int dot_batched_grid(int sm_count)

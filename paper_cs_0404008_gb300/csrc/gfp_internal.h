@@ -67,9 +67,12 @@ cudaError_t launch_fill_uniform(uint32_t p, uint64_t seed, uint64_t stream_id, u
                                 uint64_t n, uint32_t *out, cudaStream_t s);
 cudaError_t launch_check_range(const uint32_t *v, uint64_t n, uint32_t p, uint32_t *flag,
                                cudaStream_t s);
+// u non-null: also *sout = (sum_i u_i y_i) mod p, combined through slot/ticket
 cudaError_t launch_matvec(Repr r, const Mod &m, uint64_t k, uint64_t rows, uint64_t cols,
                           const uint32_t *A, uint64_t lda, const uint32_t *x, uint32_t *y,
-                          int sm_count, cudaStream_t s);
+                          int sm_count, cudaStream_t s, const uint32_t *u = nullptr,
+                          unsigned long long *slot = nullptr, uint32_t *ticket = nullptr,
+                          uint32_t *sout = nullptr);
 
 // Block product (gfp_block.cu).  The tensor-core path needs the centred
 // residues to fit two balanced 8-bit digits: (p-1)/2 <= 32895.
@@ -155,4 +158,20 @@ struct gfp_ctx {
         }
     };
     std::map<GraphKey, cudaGraphExec_t> graphs;
+    // sequence graphs (x0, u, A, ...) and their ping-pong vectors
+    struct SeqKey {
+        uint32_t p; uint64_t n; const uint32_t *A; uint64_t lda; const uint32_t *x0;
+        const uint32_t *u; uint32_t *seq; uint32_t *Y; uint32_t iters; int repr;
+        bool operator<(const SeqKey &o) const
+        {
+            return std::tie(p, n, A, lda, x0, u, seq, Y, iters, repr) <
+                   std::tie(o.p, o.n, o.A, o.lda, o.x0, o.u, o.seq, o.Y, o.iters, o.repr);
+        }
+    };
+    std::map<SeqKey, cudaGraphExec_t> seq_graphs;
+    uint32_t *pingpong = nullptr;
+    uint64_t pingpong_n = 0;
+    unsigned long long *seq_slots = nullptr;   // per-iteration projection scratch
+    uint32_t *seq_tickets = nullptr;
+    uint32_t seq_cap = 0;
 };

@@ -14,10 +14,40 @@ namespace gfp {
 
 constexpr int MV_RB = 64;   // rows per batch (multiple of every group count G)
 
+// Sum of one uint64 per thread over the CTA, valid in thread 0.
+__device__ __forceinline__ uint64_t cta_sum_mv(uint64_t v)
+{
+    __shared__ uint64_t sh[32];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;
+}
+
+// Projection of the product onto a vector u, fused into the epilogue (the
+// scalar sequence u^T A^t x of a Wiedemann-style iteration): every CTA adds
+// the residue of sum_i u_i y_i over its rows to a slot; the last CTA reduces
+// it into *sout.  Inactive when u is null.
+struct MvProj {
+    const uint32_t *u;
+    unsigned long long *slot;
+    uint32_t *ticket;
+    uint32_t *sout;
+};
+
 template <class Acc, bool XS, int U>
 __global__ void __launch_bounds__(MV_THREADS, 1)
     k_matvec(Mod m, uint64_t k, uint64_t rows, uint64_t cols, const uint32_t *__restrict__ A,
-             uint64_t lda, const uint32_t *__restrict__ x, uint32_t *__restrict__ y, int W)
+             uint64_t lda, const uint32_t *__restrict__ x, uint32_t *__restrict__ y, int W,
+             MvProj proj)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const uint64_t colsp = (cols + 3) & ~3ull;
@@ -41,6 +71,7 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
 
     const uint64_t r_begin = rows * blockIdx.x / gridDim.x;
     const uint64_t r_end = rows * (blockIdx.x + 1) / gridDim.x;
+    uint64_t pacc = 0;   // projection partial (sum of residues)
 
     for (uint64_t rb = r_begin; rb < r_end; rb += MV_RB) {
         const uint64_t rcount = (r_end - rb < (uint64_t)MV_RB) ? r_end - rb : (uint64_t)MV_RB;
@@ -80,9 +111,24 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
         for (uint64_t i = threadIdx.x; i < rcount; i += blockDim.x) {
             uint64_t s = 0;
             for (int q = 0; q < W; ++q) s += part[i * W + q];
-            y[rb + i] = reduce64(s, m);
+            const uint32_t yi = reduce64(s, m);
+            y[rb + i] = yi;
+            if (proj.u) pacc += reduce64((uint64_t)yi * __ldg(proj.u + rb + i), m);
         }
         __syncthreads();
+    }
+    if (proj.u) {
+        const uint64_t s = cta_sum_mv(pacc);
+        if (threadIdx.x == 0) {
+            atomicAdd(proj.slot, (unsigned long long)reduce64(s, m));
+            __threadfence();
+            if (atomicAdd(proj.ticket, 1u) == gridDim.x - 1) {
+                __threadfence();
+                const unsigned long long v = atomicExch(proj.slot, 0ull);
+                atomicExch(proj.ticket, 0u);
+                *proj.sout = reduce64((uint64_t)v, m);
+            }
+        }
     }
 }
 
@@ -92,7 +138,7 @@ constexpr size_t MV_XS_MAX = 200 * 1024;
 template <class Acc, bool XS>
 static cudaError_t mv_launch(const Mod &m, uint64_t k, uint64_t rows, uint64_t cols,
                              const uint32_t *A, uint64_t lda, const uint32_t *x, uint32_t *y,
-                             int sm_count, cudaStream_t s)
+                             int sm_count, cudaStream_t s, const MvProj &proj)
 {
     constexpr int U = 4;
     const int nw = MV_THREADS / 32;
@@ -113,29 +159,31 @@ static cudaError_t mv_launch(const Mod &m, uint64_t k, uint64_t rows, uint64_t c
     uint64_t grid = (uint64_t)sm_count;
     if (grid > rows) grid = rows ? rows : 1;
     k_matvec<Acc, XS, U><<<(unsigned)grid, MV_THREADS, smem, s>>>(m, k, rows, cols, A, lda, x, y,
-                                                                  W);
+                                                                  W, proj);
     return cudaGetLastError();
 }
 
 template <class Acc>
 static cudaError_t mv_dispatch(const Mod &m, uint64_t k, uint64_t rows, uint64_t cols,
                                const uint32_t *A, uint64_t lda, const uint32_t *x, uint32_t *y,
-                               int sm_count, cudaStream_t s)
+                               int sm_count, cudaStream_t s, const MvProj &proj)
 {
     if (((cols + 3) & ~3ull) * 4 <= MV_XS_MAX)
-        return mv_launch<Acc, true>(m, k, rows, cols, A, lda, x, y, sm_count, s);
-    return mv_launch<Acc, false>(m, k, rows, cols, A, lda, x, y, sm_count, s);
+        return mv_launch<Acc, true>(m, k, rows, cols, A, lda, x, y, sm_count, s, proj);
+    return mv_launch<Acc, false>(m, k, rows, cols, A, lda, x, y, sm_count, s, proj);
 }
 
 cudaError_t launch_matvec(Repr r, const Mod &m, uint64_t k, uint64_t rows, uint64_t cols,
                           const uint32_t *A, uint64_t lda, const uint32_t *x, uint32_t *y,
-                          int sm_count, cudaStream_t s)
+                          int sm_count, cudaStream_t s, const uint32_t *u,
+                          unsigned long long *slot, uint32_t *ticket, uint32_t *sout)
 {
+    const MvProj proj{u, slot, ticket, sout};
     switch (r) {
-    case U64_BLOCK: return mv_dispatch<AccBlock>(m, k, rows, cols, A, lda, x, y, sm_count, s);
-    case U64_CARRY: return mv_dispatch<AccCarry>(m, k, rows, cols, A, lda, x, y, sm_count, s);
-    case FP64: return mv_dispatch<AccF64>(m, k, rows, cols, A, lda, x, y, sm_count, s);
-    default: return mv_dispatch<AccPerTerm>(m, k, rows, cols, A, lda, x, y, sm_count, s);
+    case U64_BLOCK: return mv_dispatch<AccBlock>(m, k, rows, cols, A, lda, x, y, sm_count, s, proj);
+    case U64_CARRY: return mv_dispatch<AccCarry>(m, k, rows, cols, A, lda, x, y, sm_count, s, proj);
+    case FP64: return mv_dispatch<AccF64>(m, k, rows, cols, A, lda, x, y, sm_count, s, proj);
+    default: return mv_dispatch<AccPerTerm>(m, k, rows, cols, A, lda, x, y, sm_count, s, proj);
     }
 }
 

@@ -398,6 +398,9 @@ GFP_API gfp_status gfp_context_destroy(gfp_ctx *ctx)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : ctx->seq_graphs) cudaGraphExecDestroy(kv.second);
+    if (ctx->pingpong) cudaFree(ctx->pingpong);
+    if (ctx->seq_slots) cudaFree(ctx->seq_slots);
     for (int i = 0; i < gfp_ctx::kCopyStreams; ++i)
         if (ctx->copy_streams[i]) cudaStreamDestroy(ctx->copy_streams[i]);
     for (int i = 0; i <= gfp_ctx::kCopyStreams; ++i)
@@ -822,6 +825,80 @@ GFP_API gfp_status gfp_wait_selftest(uint64_t limit_ns, void *stream)
     uint32_t bits = 0;
     GFP_CUDA_TRY(wait_selftest(limit_ns, as_stream(stream), &bits));
     return (bits & 1u) ? GFP_ERR_TIMEOUT : GFP_OK;
+}
+
+GFP_API gfp_status gfp_matvec_sequence(gfp_ctx *ctx, uint32_t p, uint64_t n, const uint32_t *A,
+                                       uint64_t lda, const uint32_t *x0, const uint32_t *u,
+                                       uint32_t iters, uint32_t *seq, uint32_t *Y, void *stream)
+{
+    if (!ctx || p < 2 || lda < n || !seq || (n && (!A || !x0 || !u))) return GFP_ERR_INVALID;
+    if ((((uintptr_t)A) | ((uintptr_t)x0) | ((uintptr_t)u) | ((uintptr_t)seq) | ((uintptr_t)Y)) & 3u)
+        return GFP_ERR_INVALID;
+    if (iters > 65535) return GFP_ERR_INVALID;
+    cudaStream_t s = as_stream(stream);
+    if (n == 0) {
+        GFP_CUDA_TRY(cudaMemsetAsync(seq, 0, 4ull * (iters + 1), s));
+        return GFP_OK;
+    }
+    Repr r;
+    if (!resolve_repr(ctx, GFP_REPR_AUTO, p, n, &r)) return GFP_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    // scratch, grown outside any capture: projection slots and ping-pong vectors
+    if (iters + 1 > ctx->seq_cap) {
+        GFP_CUDA_TRY(cudaStreamSynchronize(s));
+        if (ctx->seq_slots) cudaFree(ctx->seq_slots);
+        ctx->seq_slots = nullptr;
+        ctx->seq_cap = 0;
+        const uint32_t cap = std::max<uint32_t>(iters + 1, 256);
+        void *mem = nullptr;
+        if (cudaMalloc(&mem, (size_t)cap * 12) != cudaSuccess) return GFP_ERR_NOMEM;
+        GFP_CUDA_TRY(cudaMemset(mem, 0, (size_t)cap * 12));
+        ctx->seq_slots = (unsigned long long *)mem;
+        ctx->seq_tickets = (uint32_t *)((char *)mem + (size_t)cap * 8);
+        ctx->seq_cap = cap;
+    }
+    if (!Y && 2 * n > ctx->pingpong_n) {
+        GFP_CUDA_TRY(cudaStreamSynchronize(s));
+        if (ctx->pingpong) cudaFree(ctx->pingpong);
+        ctx->pingpong = nullptr;
+        ctx->pingpong_n = 0;
+        if (cudaMalloc(&ctx->pingpong, 2 * n * 4) != cudaSuccess) return GFP_ERR_NOMEM;
+        ctx->pingpong_n = 2 * n;
+    }
+    gfp_ctx::SeqKey key{p, n, A, lda, x0, u, seq, Y, iters, (int)r};
+    auto it = ctx->seq_graphs.find(key);
+    if (it == ctx->seq_graphs.end()) {
+        cudaStream_t cs;
+        GFP_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        const Mod m = make_mod(p);
+        const uint64_t k = k_for(r, p);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess)
+            e = launch_dot_single(r, m, k, n, u, x0, ctx->seq_slots, ctx->seq_tickets, seq,
+                                  dot_single_grid(r, n, ctx->sm_count), cs);
+        for (uint32_t t = 1; e == cudaSuccess && t <= iters; ++t) {
+            const uint32_t *xin = (t == 1) ? x0
+                                  : (Y ? Y + (uint64_t)(t - 2) * n : ctx->pingpong + (uint64_t)(t % 2) * n);
+            uint32_t *xout = Y ? Y + (uint64_t)(t - 1) * n : ctx->pingpong + (uint64_t)((t + 1) % 2) * n;
+            e = launch_matvec(r, m, k, n, n, A, lda, xin, xout, ctx->sm_count, cs, u,
+                              ctx->seq_slots + t, ctx->seq_tickets + t, seq + t);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e2;
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) {
+            g_last_cuda_error = e;
+            return GFP_ERR_CUDA;
+        }
+        it = ctx->seq_graphs.emplace(key, exec).first;
+    }
+    GFP_CUDA_TRY(cudaGraphLaunch(it->second, s));
+    ctx->launches += iters + 1;
+    return GFP_OK;
 }
 
 GFP_API gfp_status gfp_fill_uniform(uint32_t p, uint64_t seed, uint64_t stream_id,

@@ -110,6 +110,7 @@ _SIGS = {
     "gfp_dot_batched_host": (_int, [_vp, _u64, _vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp]),
     "gfp_matvec": (_int, [_vp, _u32, _u64, _u64, _vp, _u64, _vp, _vp, _vp]),
     "gfp_matvec_iterate": (_int, [_vp, _u32, _u64, _vp, _u64, _vp, _vp, _u32, _vp]),
+    "gfp_matvec_sequence": (_int, [_vp, _u32, _u64, _vp, _u64, _vp, _vp, _u32, _vp, _vp, _vp]),
     "gfp_matmul_block": (_int, [_vp, _u32, _u64, _u64, _u64, _vp, _u64, _vp, _u64, _vp, _u64, _vp]),
     "gfp_matmul_block_csr": (_int, [_vp, _u32, _u64, _u64, _u64, _vp, _vp, _vp, _vp, _u64, _vp, _u64,
                                     _vp]),
@@ -417,6 +418,21 @@ def gfp_matvec_iterate(ctx: Context, p: int, A, x0, Y, iters: int, stream=None,
     _check(load().gfp_matvec_iterate(ctx.handle, p, n, _ptr(A), lda, _ptr(x0), _ptr(Y), iters,
                                      _stream(stream)), "gfp_matvec_iterate")
     return Y
+
+
+def gfp_matvec_sequence(ctx: Context, p: int, A, x0, u, seq, iters: int, Y=None, stream=None,
+                        lda: int | None = None):
+    """seq[t] = u^T A^t x0 mod p, t = 0..iters (device tensors)."""
+    n = A.shape[0]
+    lda = A.stride(0) if lda is None else lda
+    _check_u32(x0, n, "x0")
+    _check_u32(u, n, "u")
+    _check_u32(seq, iters + 1, "seq")
+    if Y is not None:
+        _check_u32(Y, n * iters, "Y")
+    _check(load().gfp_matvec_sequence(ctx.handle, p, n, _ptr(A), lda, _ptr(x0), _ptr(u), iters,
+                                      _ptr(seq), _ptr(Y), _stream(stream)), "gfp_matvec_sequence")
+    return seq
 
 
 # ---- block products ----

@@ -236,3 +236,27 @@ def test_validation_and_errors(lib, fresh):
     st = lib.load().gfp_dot(fresh.handle, p, 10, xd.data_ptr() + 2, xd.data_ptr(),
                             out.data_ptr(), None)
     assert st == lib.GFP_ERR_INVALID
+
+
+@pytest.mark.parametrize("p,n,iters", [(2147483647, 1024, 16), (65521, 777, 5), (4294967291, 1, 3)])
+def test_matvec_sequence_projection(lib, fresh, p, n, iters):
+    """seq[t] = u^T A^t x0: the fused projection against the oracle chain."""
+    A = gi.uniform(p, n * n, 51, 0).reshape(n, n)
+    x0 = gi.uniform(p, n, 51, 1)
+    u = gi.uniform(p, n, 51, 2)
+    want = [oracle.dot(p, u, x0)]
+    xt = x0
+    for _ in range(iters):
+        xt = oracle.matvec(p, A, xt)
+        want.append(oracle.dot(p, u, xt))
+    Ad, xd, ud = dev2(A), dev(x0), dev(u)
+    for use_y in (False, True):
+        seq = empty(iters + 1)
+        Y = empty(n * iters) if use_y else None
+        for _ in range(2):
+            seq.fill_(-1)
+            lib.gfp_matvec_sequence(fresh, p, Ad, xd, ud, seq, iters, Y=Y)
+            torch.cuda.synchronize()
+            assert host(seq)[:iters + 1].tolist() == want, use_y
+        if use_y:
+            assert int(host(Y)[(iters - 1) * n]) == int(xt[0])

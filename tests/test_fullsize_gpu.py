@@ -58,3 +58,37 @@ def test_wiedemann_iteration_full(lib, ctx):
             i = int(i)
             assert int(Yh[t][i]) == oracle.dot(p, A[i], prev), (t, i)
         prev = Yh[t]
+
+
+@pytest.mark.parametrize("repr_", [0, 1, 3])
+def test_dot_beyond_2_31_elements(lib, ctx, repr_):
+    """n > 2^31 (64-bit indexing) with all-(p-1) operands at p = 2^32-5:
+    every product wraps a 64-bit accumulator; the result is n mod p."""
+    p = 4294967291
+    n = (1 << 31) + 12345
+    ctx.set_repr(repr_)
+    try:
+        v = torch.full((n,), (p - 1) - (1 << 32), dtype=torch.int32, device="cuda")
+        out = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        lib.gfp_dot(ctx, p, v, v, out)
+        torch.cuda.synchronize()
+        assert int(host(out)[0]) == n % p
+    finally:
+        ctx.set_repr(0)
+        del v
+        torch.cuda.empty_cache()
+
+
+def test_matvec_beyond_2_31_elements(lib, ctx):
+    """A with more than 2^31 entries (64-bit row offsets), all (p-1):
+    every y_i = cols (p-1)^2 = cols (mod p)."""
+    p = 2147483647
+    rows, cols = 70001, 32768
+    A = torch.full((rows, cols), p - 1, dtype=torch.int32, device="cuda")
+    x = torch.full((cols,), p - 1, dtype=torch.int32, device="cuda")
+    y = torch.full((rows,), -1, dtype=torch.int32, device="cuda")
+    lib.gfp_matvec(ctx, p, A, x, y)
+    torch.cuda.synchronize()
+    assert (host(y) == cols % p).all()
+    del A
+    torch.cuda.empty_cache()
