@@ -42,41 +42,80 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def bind(lib):
+    """Declare the C signatures on a loaded oracle library (used for the
+    default build and, by the tests, for deliberately broken variants)."""
+    lib.oracle_dot.restype = ctypes.c_uint32
+    lib.oracle_dot.argtypes = [ctypes.c_uint32, ctypes.c_uint64, _u32p, _u32p]
+    lib.oracle_dot_batch.restype = None
+    lib.oracle_dot_batch.argtypes = [ctypes.c_uint64, _u32p, _u64p, _u64p, _u32p, _u32p, _u32p]
+    lib.oracle_matvec_rows.restype = None
+    lib.oracle_matvec_rows.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                       ctypes.c_uint64, _u32p, ctypes.c_uint64, _u32p, _u32p]
+    lib.oracle_block_rows.restype = None
+    lib.oracle_block_rows.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                      ctypes.c_uint64, ctypes.c_uint64, _u32p, ctypes.c_uint64,
+                                      _u32p, ctypes.c_uint64, _u32p, ctypes.c_uint64]
+    lib.oracle_csr_rows.restype = None
+    lib.oracle_csr_rows.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                    ctypes.c_uint64, _u32p, _u32p, _u32p, _u32p, ctypes.c_uint64,
+                                    _u32p, ctypes.c_uint64]
+    lib.oracle_paper_block_dot.restype = ctypes.c_uint64
+    lib.oracle_paper_block_dot.argtypes = [ctypes.c_uint32, ctypes.c_uint64, _u32p, _u32p,
+                                           ctypes.c_uint64, ctypes.c_int]
+    lib.oracle_paper_overflow_dot.restype = ctypes.c_uint32
+    lib.oracle_paper_overflow_dot.argtypes = [ctypes.c_uint32, ctypes.c_uint64, _u32p, _u32p]
+    lib.oracle_paper_fp_reduce.restype = ctypes.c_double
+    lib.oracle_paper_fp_reduce.argtypes = [ctypes.c_double, ctypes.c_double]
+    lib.oracle_paper_fp_dot.restype = ctypes.c_uint32
+    lib.oracle_paper_fp_dot.argtypes = [ctypes.c_uint32, ctypes.c_uint64, _u32p, _u32p,
+                                        ctypes.c_uint64]
+    return lib
+
+
+def compile_variant(source: str, out_dir: str, name: str):
+    """Compile an edited copy of the oracle source (tests plant mistakes in
+    copies to check that the pins catch them) and return the bound library."""
+    src = os.path.join(out_dir, name + ".c")
+    so = os.path.join(out_dir, name + ".so")
+    with open(src, "w") as f:
+        f.write(source)
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", so, src, "-lm"], check=True)
+    return bind(ctypes.CDLL(so))
+
+
+def source() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+_override = threading.local()
+
+
+class use:
+    """Context manager: route this thread's oracle calls to another bound
+    library (a planted-mistake variant in the tests)."""
+
+    def __init__(self, lib):
+        self.lib = lib
+
+    def __enter__(self):
+        self.prev = getattr(_override, "lib", None)
+        _override.lib = self.lib
+        return self
+
+    def __exit__(self, *exc):
+        _override.lib = self.prev
+
+
 def _load():
     global _lib
+    ov = getattr(_override, "lib", None)
+    if ov is not None:
+        return ov
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            lib.oracle_dot.restype = ctypes.c_uint32
-            lib.oracle_dot.argtypes = [ctypes.c_uint32, ctypes.c_uint64, _u32p, _u32p]
-            lib.oracle_dot_batch.restype = None
-            lib.oracle_dot_batch.argtypes = [ctypes.c_uint64, _u32p, _u64p, _u64p, _u32p, _u32p,
-                                             _u32p]
-            lib.oracle_matvec_rows.restype = None
-            lib.oracle_matvec_rows.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
-                                               ctypes.c_uint64, _u32p, ctypes.c_uint64, _u32p,
-                                               _u32p]
-            lib.oracle_block_rows.restype = None
-            lib.oracle_block_rows.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
-                                              ctypes.c_uint64, ctypes.c_uint64, _u32p,
-                                              ctypes.c_uint64, _u32p, ctypes.c_uint64, _u32p,
-                                              ctypes.c_uint64]
-            lib.oracle_csr_rows.restype = None
-            lib.oracle_csr_rows.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
-                                            ctypes.c_uint64, _u32p, _u32p, _u32p, _u32p,
-                                            ctypes.c_uint64, _u32p, ctypes.c_uint64]
-            lib.oracle_paper_block_dot.restype = ctypes.c_uint64
-            lib.oracle_paper_block_dot.argtypes = [ctypes.c_uint32, ctypes.c_uint64, _u32p, _u32p,
-                                                   ctypes.c_uint64, ctypes.c_int]
-            lib.oracle_paper_overflow_dot.restype = ctypes.c_uint32
-            lib.oracle_paper_overflow_dot.argtypes = [ctypes.c_uint32, ctypes.c_uint64, _u32p,
-                                                      _u32p]
-            lib.oracle_paper_fp_reduce.restype = ctypes.c_double
-            lib.oracle_paper_fp_reduce.argtypes = [ctypes.c_double, ctypes.c_double]
-            lib.oracle_paper_fp_dot.restype = ctypes.c_uint32
-            lib.oracle_paper_fp_dot.argtypes = [ctypes.c_uint32, ctypes.c_uint64, _u32p, _u32p,
-                                                ctypes.c_uint64]
-            _lib = lib
+            _lib = bind(ctypes.CDLL(build()))
     return _lib
 
 
