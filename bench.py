@@ -351,6 +351,26 @@ def run_gpu(args):
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline()
 
+    # the other workloads, measured after the timed region (one GPU, rank 0)
+    also = None
+    if rank == 0 and world == 1 and not args.quick and not args.no_also:
+        also = {}
+        plan.close()
+        plan._keep = None
+        batch.x = batch.y = None
+        torch.cuda.empty_cache()
+        for name in ("dot", "matvec", "block", "csr"):
+            ln = measure_secondary(args, name, g, torch, ctx, stream)
+            also[name] = {k: ln[k] for k in ("value", "unit", "ms_per_step", "config", "roofline")
+                          if k in ln}
+            for k in ("single_call_us", "graph_of_256_single_dots", "same_gpu"):
+                if k in ln:
+                    also[name][k] = ln[k]
+            torch.cuda.empty_cache()
+        sv = measure_serve(args, g)
+        also["serve"] = {"value": sv["value"], "unit": sv["unit"], "config": sv["config"],
+                         **sv["serve"]}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -375,6 +395,7 @@ def run_gpu(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "same_gpu": extra,
+            "also": also,
         }
         print(json.dumps(line), flush=True)
     plan.close()
@@ -421,11 +442,18 @@ def run_secondary(args):
     g.load()
     ctx = g.Context(0)
     stream = torch.cuda.Stream()
+    line = measure_secondary(args, args.workload, g, torch, ctx, stream)
+    ctx.close()
+    print(json.dumps(line), flush=True)
+
+
+def measure_secondary(args, workload, g, torch, ctx, stream):
+    """One secondary workload on an existing context; returns its JSON line."""
     peak, peak_kind = hbm_peak()
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic"}
-    if args.workload == "dot":
+    if workload == "dot":
         p, n, nvec = 65521, 1 << 20, 256
         seed = gi.BASE_SEED
         # 256 operand pairs on rotating buffers: 2 GiB, larger than L2
@@ -489,7 +517,7 @@ def run_secondary(args):
             "gpu_launches": len(per),
         })
         plan.close()
-    elif args.workload == "matvec":
+    elif workload == "matvec":
         p, n, iters = 2147483647, args.mv_n, args.mv_iters
         A = torch.empty((n, n), dtype=torch.int32, device="cuda")
         g.gfp_fill_uniform(p, gi.BASE_SEED + 2, 0, A)
@@ -528,7 +556,7 @@ def run_secondary(args):
                          "speedup_over_perterm": res["perterm"] / t},
             "gpu_launches": iters,
         })
-    elif args.workload in ("block", "csr"):
+    elif workload in ("block", "csr"):
         p, m, k, nb = 65521, args.block_m, 16384, 64
         seed = gi.BASE_SEED + 3
         B = torch.empty((k, nb), dtype=torch.int32, device="cuda")
@@ -549,7 +577,7 @@ def run_secondary(args):
             torch.cuda.synchronize()
             return e0.elapsed_time(e1) / reps
 
-        if args.workload == "block":
+        if workload == "block":
             A = torch.empty((m, k), dtype=torch.int32, device="cuda")
             g.gfp_fill_uniform(p, seed, 0, A)
             res = {}
@@ -598,8 +626,8 @@ def run_secondary(args):
                              "note": "B (4 MiB) is re-read from L2 per nonzero; HBM bytes count it once"},
                 "gpu_launches": 1,
             })
-    ctx.close()
-    print(json.dumps(line), flush=True)
+    torch.cuda.synchronize()
+    return line
 
 
 # ---------------------------------------------------------------------------
@@ -626,13 +654,17 @@ def serve_requests(count: int, seed: int):
 
 
 def run_serve(args):
-    import threading as th
     import torch
     from paper_cs_0404008_gb300 import gfpdot as g
-    import oracle
-
     torch.cuda.set_device(0)
     g.load()
+    print(json.dumps(measure_serve(args, g)), flush=True)
+
+
+def measure_serve(args, g):
+    import threading as th
+    import oracle
+
     seed = gi.BASE_SEED + 5
     srv = g.Server(device=0, mem_budget=16 << 30, n_streams=8, batch_window_us=50,
                    max_inflight=256)
@@ -768,7 +800,7 @@ def run_serve(args):
                   "mem_peak_bytes": stats1["mem_peak"]},
         "gpu_launches": stats1["kernel_launches"] - stats0["kernel_launches"],
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -780,6 +812,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the per-representation comparisons")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-also", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-tune", action="store_true", help="built-in representation rules")
     ap.add_argument("--no-clocks", action="store_true", help="skip the clock-sampling load phase")
     ap.add_argument("--pairs", type=int, default=COUNT, help="batch size (smaller for profiling)")
