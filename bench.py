@@ -307,6 +307,8 @@ def run_gpu(args):
     if not args.quick:
         for name, rp, mask in (("perterm", g.GFP_REPR_PERTERM, None),
                                ("u64_carry", g.GFP_REPR_U64_CARRY, None),
+                               ("centered", g.GFP_REPR_CENTERED, None),
+                               ("montgomery", g.GFP_REPR_MONTGOMERY, None),
                                ("fp64_p_lt_2^26", g.GFP_REPR_FP64, batch.ps < (1 << 26))):
             pl = g.BatchPlan(ctx, batch.pairs(rp, mask))
             sel = batch.lens if mask is None else batch.lens[mask]

@@ -76,7 +76,13 @@ typedef enum gfp_repr {
     GFP_REPR_F16TC = 5,     /* block product only: centred residues (Section 3.2.2) split into
                                two balanced 8-bit digits, exact fp16 tensor-core products with
                                fp32 accumulation over chunks of 1024 terms (p <= 65791) */
-    GFP_REPR_COUNT_ = 6
+    GFP_REPR_CENTERED = 6,  /* centred representation (Section 3.2.2): signed residues in
+                               [-(p-1)/2, (p-1)/2], signed 64-bit accumulator reduced every
+                               k terms, k h^2 + (p-1) <= 2^63 - 1 with h = (p-1)/2 */
+    GFP_REPR_MONTGOMERY = 7,/* Montgomery reduction (Sections 2.2, 3.2.1), B = 2^32, odd p:
+                               blocks of k products with k (p-1)^2 < p B reduced by REDC,
+                               the B^-1 factor removed once at the end */
+    GFP_REPR_COUNT_ = 8
 } gfp_repr;
 
 typedef struct gfp_ctx gfp_ctx;
@@ -90,6 +96,8 @@ typedef struct gfp_params {
     uint64_t barrett_mu;  /* floor(2^64 / p), Barrett's reduction constant */
     double   inv_p;       /* 1/p rounded to double (Section 2.3) */
     int      fp64_ok;     /* 1 when k_fp64 >= 1 */
+    uint64_t k_centered;  /* GFP_REPR_CENTERED block length (see gfp_repr) */
+    uint64_t k_montgomery;/* GFP_REPR_MONTGOMERY block length; 0 for even p */
 } gfp_params;
 
 /* ---- status and parameters (host only; usable without a GPU) ---- */
@@ -289,7 +297,8 @@ GFP_API gfp_status gfp_wait_selftest(uint64_t limit_ns, void *stream);
 
 /* ---- install-time tuning (automated empirical optimisation, Section 4) ---- */
 
-/* Time every eligible representation (U64_BLOCK, U64_CARRY, FP64) and
+/* Time every eligible representation (U64_BLOCK, U64_CARRY, FP64, CENTERED,
+ * MONTGOMERY) and
  * work-unit length (16Ki, 64Ki, 256Ki elements) for each prime of
  * primes[0..nprimes) (NULL: 32749, 65521, 67108859, 2^31-1, 2^32-5) and
  * each length 2^lg, lg = lg_lo, lg_lo+2, ..., <= lg_hi (lg_hi <= 26), on

@@ -16,7 +16,9 @@
 
 namespace gfp {
 
-enum Repr : uint32_t { PERTERM = 1, U64_BLOCK = 2, U64_CARRY = 3, FP64 = 4 };
+enum Repr : uint32_t {
+    PERTERM = 1, U64_BLOCK = 2, U64_CARRY = 3, FP64 = 4, CENTERED = 6, MONTGOMERY = 7
+};
 
 // Constants for one modulus p (2 <= p <= 2^32-1).
 struct Mod {
@@ -174,6 +176,98 @@ struct AccF64 {
         }
     }
     GFP_D uint32_t residue(const Mod &m) const { return (uint32_t)reduce_f64(acc, m); }
+};
+
+// Centred representation (Section 3.2.2): residues are read as
+// s in [-(p-1)/2, (p-1)/2] and signed products accumulate in 64 bits; with
+// h = (p-1)/2 the block bound is k h^2 + (p-1) <= 2^63 - 1, about twice the
+// unsigned Eq. (2) block for the same modulus.  Reduction of a signed sum
+// into [0, p) uses the Barrett reduction of its magnitude.
+struct AccCentered {
+    long long acc;
+    uint64_t left, k;
+    GFP_D void init(const Mod &, uint64_t kk) { acc = 0; k = kk; left = kk; }
+    static GFP_D long long centre(uint32_t a, const Mod &m)
+    {
+        return (a > ((m.p - 1) >> 1)) ? (long long)a - (long long)m.p : (long long)a;
+    }
+    static GFP_D uint32_t residue_of(long long v, const Mod &m)
+    {
+        if (v >= 0) return reduce64((uint64_t)v, m);
+        const uint32_t t = reduce64((uint64_t)(-v), m);
+        return t ? m.p - t : 0u;
+    }
+    GFP_D void add(uint32_t a, uint32_t b, const Mod &m)
+    {
+        if (left == 0) { acc = (long long)residue_of(acc, m); left = k; }
+        acc += centre(a, m) * centre(b, m);
+        --left;
+    }
+    GFP_D void add4(uint4 a, uint4 b, const Mod &m)
+    {
+        if (left >= 4) {
+            acc += centre(a.x, m) * centre(b.x, m);
+            acc += centre(a.y, m) * centre(b.y, m);
+            acc += centre(a.z, m) * centre(b.z, m);
+            acc += centre(a.w, m) * centre(b.w, m);
+            left -= 4;
+        } else {
+            add(a.x, b.x, m); add(a.y, b.y, m); add(a.z, b.z, m); add(a.w, b.w, m);
+        }
+    }
+    GFP_D uint32_t residue(const Mod &m) const { return residue_of(acc, m); }
+};
+
+// Montgomery reduction (Section 2.2; blocked as in Section 3.2.1) with
+// B = 2^32 for odd p: a block of products T < pB is reduced by
+// REDC(T) = T B^-1 mod p (Montgomery, Math. Comp. 1985), the block results
+// are summed, and the total, which carries a factor B^-1, is multiplied back
+// by REDC(total * (B^2 mod p)).  B^2 mod p = 2^64 mod p is the CORR constant.
+struct AccMontgomery {
+    uint64_t acc, sum;
+    uint64_t left, k;
+    uint32_t ninv;   // -p^-1 mod 2^32
+    GFP_D void init(const Mod &m, uint64_t kk)
+    {
+        acc = 0; sum = 0; k = kk; left = kk;
+        uint32_t x = m.p;                       // p^-1 mod 2^32 by Newton's iteration
+        for (int i = 0; i < 5; ++i) x *= 2u - m.p * x;
+        ninv = 0u - x;
+    }
+    GFP_D uint32_t redc(uint64_t T, const Mod &m) const
+    {
+        const uint32_t lo = (uint32_t)T;
+        const uint32_t q = lo * ninv;           // T + q p = 0 (mod 2^32)
+        // (T + q p) / 2^32 without the 65-bit sum: the low words cancel exactly
+        uint64_t t = (T >> 32) + (uint64_t)(((uint64_t)q * m.p) >> 32) + (lo != 0u ? 1u : 0u);
+        if (t >= m.p) t -= m.p;
+        return (uint32_t)t;
+    }
+    GFP_D void flush(const Mod &m) { sum += redc(acc, m); acc = 0; left = k; }
+    GFP_D void add(uint32_t a, uint32_t b, const Mod &m)
+    {
+        if (left == 0) flush(m);
+        acc += (uint64_t)a * b;
+        --left;
+    }
+    GFP_D void add4(uint4 a, uint4 b, const Mod &m)
+    {
+        if (left >= 4) {
+            acc += (uint64_t)a.x * b.x;
+            acc += (uint64_t)a.y * b.y;
+            acc += (uint64_t)a.z * b.z;
+            acc += (uint64_t)a.w * b.w;
+            left -= 4;
+        } else {
+            add(a.x, b.x, m); add(a.y, b.y, m); add(a.z, b.z, m); add(a.w, b.w, m);
+        }
+    }
+    GFP_D uint32_t residue(const Mod &m) const
+    {
+        // sum < (blocks + 1) p; reduce, then multiply back by B: REDC(x * B^2 mod p) = x B
+        const uint64_t total = (uint64_t)reduce64(sum + redc(acc, m), m);
+        return redc(total * m.corr, m);
+    }
 };
 
 }  // namespace gfp

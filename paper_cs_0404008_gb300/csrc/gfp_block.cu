@@ -765,6 +765,8 @@ cudaError_t launch_block_cc(Repr r, const Mod &mod, uint64_t kbound, uint64_t m,
     case U64_BLOCK: return cc_launch<AccBlock>(mod, kbound, m, k, nb, A, lda, B, ldb, C, ldc, s);
     case U64_CARRY: return cc_launch<AccCarry>(mod, kbound, m, k, nb, A, lda, B, ldb, C, ldc, s);
     case FP64: return cc_launch<AccF64>(mod, kbound, m, k, nb, A, lda, B, ldb, C, ldc, s);
+    case CENTERED: return cc_launch<AccCentered>(mod, kbound, m, k, nb, A, lda, B, ldb, C, ldc, s);
+    case MONTGOMERY: return cc_launch<AccMontgomery>(mod, kbound, m, k, nb, A, lda, B, ldb, C, ldc, s);
     default: return cc_launch<AccPerTerm>(mod, kbound, m, k, nb, A, lda, B, ldb, C, ldc, s);
     }
 }

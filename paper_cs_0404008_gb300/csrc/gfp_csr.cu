@@ -107,6 +107,10 @@ cudaError_t launch_block_csr(Repr r, const Mod &mod, uint64_t kbound, uint64_t m
         return csr_launch<AccCarry>(mod, kbound, m, k, nb, row_ptr, col, val, B, ldb, C, ldc, sm_count, s);
     case FP64:
         return csr_launch<AccF64>(mod, kbound, m, k, nb, row_ptr, col, val, B, ldb, C, ldc, sm_count, s);
+    case CENTERED:
+        return csr_launch<AccCentered>(mod, kbound, m, k, nb, row_ptr, col, val, B, ldb, C, ldc, sm_count, s);
+    case MONTGOMERY:
+        return csr_launch<AccMontgomery>(mod, kbound, m, k, nb, row_ptr, col, val, B, ldb, C, ldc, sm_count, s);
     default:
         return csr_launch<AccPerTerm>(mod, kbound, m, k, nb, row_ptr, col, val, B, ldb, C, ldc, sm_count, s);
     }

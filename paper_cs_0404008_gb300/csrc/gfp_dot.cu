@@ -150,6 +150,8 @@ __global__ void __launch_bounds__(DOT_THREADS)
         case U64_BLOCK: r = unit_residue<AccBlock>(pr, un); break;
         case U64_CARRY: r = unit_residue<AccCarry>(pr, un); break;
         case FP64: r = unit_residue<AccF64>(pr, un); break;
+        case CENTERED: r = unit_residue<AccCentered>(pr, un); break;
+        case MONTGOMERY: r = unit_residue<AccMontgomery>(pr, un); break;
         default: r = unit_residue<AccPerTerm>(pr, un); break;
         }
         const uint64_t s = cta_sum(r);   // its barriers also order the reuse of s_u
@@ -215,6 +217,8 @@ static int occupancy_for(Repr r)
     case U64_BLOCK: return occupancy_single<AccBlock>();
     case U64_CARRY: return occupancy_single<AccCarry>();
     case FP64: return occupancy_single<AccF64>();
+    case CENTERED: return occupancy_single<AccCentered>();
+    case MONTGOMERY: return occupancy_single<AccMontgomery>();
     default: return occupancy_single<AccPerTerm>();
     }
 }
@@ -255,6 +259,8 @@ cudaError_t launch_dot_single(Repr r, const Mod &m, uint64_t k, uint64_t n, cons
     case U64_BLOCK: e = launch_single_pdl<AccBlock>(m, k, n, x, y, slot, ticket, out, grid, s); break;
     case U64_CARRY: e = launch_single_pdl<AccCarry>(m, k, n, x, y, slot, ticket, out, grid, s); break;
     case FP64: e = launch_single_pdl<AccF64>(m, k, n, x, y, slot, ticket, out, grid, s); break;
+    case CENTERED: e = launch_single_pdl<AccCentered>(m, k, n, x, y, slot, ticket, out, grid, s); break;
+    case MONTGOMERY: e = launch_single_pdl<AccMontgomery>(m, k, n, x, y, slot, ticket, out, grid, s); break;
     default: e = launch_single_pdl<AccPerTerm>(m, k, n, x, y, slot, ticket, out, grid, s); break;
     }
     return e != cudaSuccess ? e : cudaGetLastError();

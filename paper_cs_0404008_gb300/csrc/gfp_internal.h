@@ -41,6 +41,8 @@ struct DevUnit {
 Mod make_mod(uint32_t p);
 uint64_t delay_bound(uint32_t p, int acc_bits, int carried);
 uint64_t k_for(Repr r, uint32_t p);
+uint64_t centered_bound(uint32_t p);
+uint64_t montgomery_bound(uint32_t p);
 bool repr_eligible(Repr r, uint32_t p);
 
 // Launch configuration constants of the dot kernels.

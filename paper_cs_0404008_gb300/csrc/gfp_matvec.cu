@@ -183,6 +183,8 @@ cudaError_t launch_matvec(Repr r, const Mod &m, uint64_t k, uint64_t rows, uint6
     case U64_BLOCK: return mv_dispatch<AccBlock>(m, k, rows, cols, A, lda, x, y, sm_count, s, proj);
     case U64_CARRY: return mv_dispatch<AccCarry>(m, k, rows, cols, A, lda, x, y, sm_count, s, proj);
     case FP64: return mv_dispatch<AccF64>(m, k, rows, cols, A, lda, x, y, sm_count, s, proj);
+    case CENTERED: return mv_dispatch<AccCentered>(m, k, rows, cols, A, lda, x, y, sm_count, s, proj);
+    case MONTGOMERY: return mv_dispatch<AccMontgomery>(m, k, rows, cols, A, lda, x, y, sm_count, s, proj);
     default: return mv_dispatch<AccPerTerm>(m, k, rows, cols, A, lda, x, y, sm_count, s, proj);
     }
 }

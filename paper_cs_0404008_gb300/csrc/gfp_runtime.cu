@@ -43,11 +43,36 @@ Mod make_mod(uint32_t p)
     return m;
 }
 
+// Centred accumulator (Section 3.2.2): largest k with k h^2 + (p-1) <= 2^63 - 1,
+// h = (p-1)/2 (a carried residue in [0, p) plus k signed products).
+uint64_t centered_bound(uint32_t p)
+{
+    if (p < 2) return 0;
+    typedef unsigned __int128 u128;
+    const u128 h = (u128)((p - 1) / 2), sq = h * h, lim = ((u128)1 << 63) - 1 - (u128)(p - 1);
+    if (sq == 0) return UINT64_MAX;
+    const u128 k = lim / sq;
+    return k > (u128)UINT64_MAX ? UINT64_MAX : (uint64_t)k;
+}
+
+// Montgomery blocks (Sections 2.2, 3.2.1) with B = 2^32: a block sum T of k
+// products must stay below p B for REDC: largest k with k (p-1)^2 < p 2^32.
+uint64_t montgomery_bound(uint32_t p)
+{
+    if (p < 3 || (p & 1u) == 0) return 0;
+    typedef unsigned __int128 u128;
+    const u128 sq = (u128)(p - 1) * (p - 1), lim = ((u128)p << 32) - 1;
+    const u128 k = lim / sq;
+    return k > (u128)UINT64_MAX ? UINT64_MAX : (uint64_t)k;
+}
+
 uint64_t k_for(Repr r, uint32_t p)
 {
     switch (r) {
     case U64_BLOCK: return delay_bound(p, 64, 1);
     case FP64: return delay_bound(p, 53, 1);
+    case CENTERED: return centered_bound(p);
+    case MONTGOMERY: return montgomery_bound(p);
     default: return 0;
     }
 }
@@ -60,6 +85,8 @@ bool repr_eligible(Repr r, uint32_t p)
     case U64_CARRY: return true;
     case U64_BLOCK: return delay_bound(p, 64, 1) >= 1;
     case FP64: return delay_bound(p, 53, 1) >= 1;
+    case CENTERED: return centered_bound(p) >= 1;
+    case MONTGOMERY: return montgomery_bound(p) >= 1;
     default: return false;
     }
 }
@@ -125,7 +152,7 @@ static bool resolve_repr(const gfp_ctx *ctx, uint32_t requested, uint32_t p, uin
         const gfp_plan_entry *e = plan_lookup(ctx, p, n);
         r = (e && repr_eligible((Repr)e->repr, p)) ? e->repr : default_repr(p);
     }
-    if (r < GFP_REPR_PERTERM || r >= GFP_REPR_COUNT_) return false;
+    if (r < GFP_REPR_PERTERM || r >= GFP_REPR_COUNT_ || r == GFP_REPR_F16TC) return false;
     if (!repr_eligible((Repr)r, p)) return false;
     *out = (Repr)r;
     return true;
@@ -172,6 +199,8 @@ double repr_cost(Repr r)
     switch (r) {
     case FP64: return 8.0;
     case PERTERM: return 6.0;
+    case CENTERED:
+    case MONTGOMERY: return 1.5;
     default: return 1.0;
     }
 }
@@ -327,6 +356,8 @@ GFP_API gfp_status gfp_get_params(uint32_t p, gfp_params *out)
     out->barrett_mu = m.mu;
     out->inv_p = m.invp;
     out->fp64_ok = out->k_fp64 >= 1;
+    out->k_centered = centered_bound(p);
+    out->k_montgomery = montgomery_bound(p);
     return GFP_OK;
 }
 

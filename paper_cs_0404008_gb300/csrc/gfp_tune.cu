@@ -121,7 +121,8 @@ GFP_API gfp_status gfp_tune(gfp_ctx *ctx, const uint32_t *primes, uint32_t nprim
     std::map<std::pair<uint32_t, uint32_t>, gfp_plan_entry> table;
     gfp_status result = GFP_OK;
     static const uint32_t chunks[] = {16384u, 65536u, 262144u};
-    static const uint32_t reprs[] = {GFP_REPR_U64_BLOCK, GFP_REPR_U64_CARRY, GFP_REPR_FP64};
+    static const uint32_t reprs[] = {GFP_REPR_U64_BLOCK, GFP_REPR_U64_CARRY, GFP_REPR_FP64,
+                                     GFP_REPR_CENTERED, GFP_REPR_MONTGOMERY};
     for (uint32_t pi = 0; pi < nprimes && result == GFP_OK; ++pi) {
         const uint32_t p = primes[pi];
         gfp_fill_uniform(p, 0x7157ull, 0, 0, pool_elems, (uint32_t *)xb.p, s);

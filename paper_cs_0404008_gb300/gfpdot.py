@@ -32,7 +32,10 @@ GFP_REPR_U64_BLOCK = 2
 GFP_REPR_U64_CARRY = 3
 GFP_REPR_FP64 = 4
 GFP_REPR_F16TC = 5
-REPR_NAMES = {0: "auto", 1: "perterm", 2: "u64_block", 3: "u64_carry", 4: "fp64", 5: "f16tc"}
+GFP_REPR_CENTERED = 6
+GFP_REPR_MONTGOMERY = 7
+REPR_NAMES = {0: "auto", 1: "perterm", 2: "u64_block", 3: "u64_carry", 4: "fp64", 5: "f16tc",
+              6: "centered", 7: "montgomery"}
 
 _vp = ctypes.c_void_p
 _u32 = ctypes.c_uint32
@@ -51,7 +54,8 @@ class GfpError(RuntimeError):
 
 class gfp_params(ctypes.Structure):
     _fields_ = [("p", _u32), ("corr", _u32), ("k_u64", _u64), ("k_fp64", _u64),
-                ("barrett_mu", _u64), ("inv_p", ctypes.c_double), ("fp64_ok", _int)]
+                ("barrett_mu", _u64), ("inv_p", ctypes.c_double), ("fp64_ok", _int),
+                ("k_centered", _u64), ("k_montgomery", _u64)]
 
 
 class gfp_dot_desc(ctypes.Structure):

@@ -98,7 +98,7 @@ def test_block_auto_path_and_unsupported(lib, fresh):
     assert ei.value.status == lib.GFP_ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("repr_", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("repr_", [0, 1, 2, 3, 4, 6, 7])
 @pytest.mark.parametrize("p", [65521, 67108859, 2147483647, 4294967291])
 def test_block_cuda_core_parity(lib, fresh, p, repr_):
     if repr_ == lib.GFP_REPR_FP64 and not lib.gfp_get_params(p)["fp64_ok"]:
@@ -132,7 +132,7 @@ def test_block_full_size_workload(lib, fresh):
     assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("repr_", [0, 1, 2, 3])
+@pytest.mark.parametrize("repr_", [0, 1, 2, 3, 6, 7])
 def test_csr_parity(lib, fresh, repr_):
     fresh.set_repr(repr_)
     for p in (65521, 4294967291):

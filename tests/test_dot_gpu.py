@@ -11,11 +11,16 @@ from gpu_util import dev, dev2, empty, host
 pytestmark = pytest.mark.gpu
 
 PRIMES = [2, 3, 7, 251, 32749, 65521, 67108859, 2147483647, 4294967291]
-REPRS = [1, 2, 3, 4]   # PERTERM, U64_BLOCK, U64_CARRY, FP64
+REPRS = [1, 2, 3, 4, 6, 7]   # PERTERM, U64_BLOCK, U64_CARRY, FP64, CENTERED, MONTGOMERY
 
 
 def eligible(lib, repr_, p):
-    return repr_ != lib.GFP_REPR_FP64 or lib.gfp_get_params(p)["fp64_ok"]
+    prm = lib.gfp_get_params(p)
+    if repr_ == lib.GFP_REPR_FP64:
+        return bool(prm["fp64_ok"])
+    if repr_ == lib.GFP_REPR_MONTGOMERY:
+        return prm["k_montgomery"] > 0
+    return True
 
 
 @pytest.fixture
@@ -162,7 +167,7 @@ def test_batched_host_buffers(lib, fresh):
     assert (oh.numpy().view(np.uint32)[:10] == want[:10]).all()
 
 
-@pytest.mark.parametrize("repr_", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("repr_", [0, 1, 2, 3, 4, 6, 7])
 @pytest.mark.parametrize("shape", [(1, 1), (7, 13), (100, 1000), (129, 4097), (300, 32768),
                                    (33, 60000)])
 def test_matvec_parity(lib, fresh, shape, repr_):

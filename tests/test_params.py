@@ -196,3 +196,25 @@ def test_fp_reduction_edges(lib, p):
     for _ in range(3000):
         T = rng.randrange(0, (1 << 53) + 1)
         assert lib.gfp_reduce_f64(float(T), p) == float(T % p)
+
+
+@pytest.mark.parametrize("p", [2, 3, 13, 32749, 65521, 67108859, 2147483647, 4294967291])
+def test_centered_and_montgomery_bounds(lib, p):
+    """Section 3.2.2: the centred block (k h^2 + (p-1) <= 2^63 - 1, h = (p-1)/2)
+    is about twice the unsigned one; Sections 2.2/3.2.1 with B = 2^32: a
+    Montgomery block of k products must stay below p B."""
+    prm = lib.gfp_get_params(p)
+    h = (p - 1) // 2
+    kc = prm["k_centered"]
+    if h:
+        assert kc * h * h + (p - 1) <= (1 << 63) - 1 < (kc + 1) * h * h + (p - 1)
+        ku = prm["k_u64"]
+        if ku < (1 << 62):
+            assert kc >= 2 * ku - 1
+    km = prm["k_montgomery"]
+    if p % 2 == 0:
+        assert km == 0
+    else:
+        assert km * (p - 1) ** 2 < p << 32 <= (km + 1) * (p - 1) ** 2
+    if p == 2147483647:
+        assert (prm["k_u64"], kc, km) == (4, 8, 2)   # centred doubles the block
