@@ -418,14 +418,18 @@ def cpu_baseline():
     lens_s, ps_s = lens[sel], ps[sel]
     off, total, x, y = gi.batched_operands(lens_s, ps_s, SEED)
     oracle.dot_batch(ps_s[:64], lens_s[:64], off[:64], x, y, threads=cores)
-    reps = 3
+    # repeat the sample until about 1 s of wall time (roughly 10-30 s of CPU
+    # work on the host cores), at least 3 times
+    reps = 0
     t0 = time.perf_counter()
-    for _ in range(reps):
+    while reps < 3 or (time.perf_counter() - t0 < 1.0 and reps < 40):
         oracle.dot_batch(ps_s, lens_s, off, x, y, threads=cores)
+        reps += 1
     dt = time.perf_counter() - t0
     macs = float(lens_s.sum()) * reps
     return {"value": macs / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"every 4th pair of the batch ({len(sel)} pairs, {lens_s.sum():.3e} MACs) x {reps}"}
+            "sample": f"every 4th pair of the batch ({len(sel)} pairs, {lens_s.sum():.3e} MACs) "
+                      f"x {reps} repetitions, {dt:.2f} s wall on {cores} threads"}
 
 
 # ---------------------------------------------------------------------------
