@@ -120,6 +120,17 @@ def test_block_k_zero_writes_zeros(lib, fresh):
     assert (host(C) == 0).all()
 
 
+def test_block_many_units_per_cta(lib, fresh):
+    """4096 x 16384 x 64: 32 row tiles x 32 exact chunks, several (tile,
+    chunk) units per persistent CTA, so shared-memory slots, TMEM stages and
+    accumulator sets are reused many times within one launch."""
+    p, m, k, nb = 65521, 4096, 16384, 64
+    A = gi.uniform(p, m * k, 65, 0).reshape(m, k)
+    B = gi.uniform(p, k * nb, 65, 1).reshape(k, nb)
+    for _ in range(2):
+        assert np.array_equal(run_block(lib, fresh, p, A, B), oracle.block(p, A, B))
+
+
 def test_block_full_size_workload(lib, fresh):
     """The block workload: A 16384 x 16384, B 16384 x 64 over GF(65521),
     tensor-core path, every entry against the oracle."""
