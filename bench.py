@@ -809,6 +809,115 @@ def measure_serve(args, g):
     return line
 
 
+# ---------------------------------------------------------------------------
+# Host representation sweep (the paper's CPU comparison, Section 3)
+# ---------------------------------------------------------------------------
+
+SWEEP_SEED = gi.BASE_SEED + 6
+SWEEP_N = 512   # the vector length of the paper's comparison
+SWEEP_PAPER_PRIMES_32 = [2887, 2897, 2903, 32749, 40009, 40499, 46337, 65521]
+SWEEP_PAPER_PRIMES_64 = [94906249, 2147483647, 3037000493, 4294967291]
+
+
+def is_prime(n: int) -> bool:
+    """Deterministic Miller-Rabin for n < 3.3e24 (bases 2..41)."""
+    if n < 2:
+        return False
+    small = (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41)
+    for q in small:
+        if n % q == 0:
+            return n == q
+    d, r = n - 1, 0
+    while d % 2 == 0:
+        d //= 2
+        r += 1
+    for a in small:
+        x = pow(a, d, n)
+        if x in (1, n - 1):
+            continue
+        for _ in range(r - 1):
+            x = x * x % n
+            if x == n - 1:
+                break
+        else:
+            return False
+    return True
+
+
+def sweep_primes(lo: int, hi: int, count: int):
+    """The largest prime at or below each of `count` log-spaced points of [lo, hi]."""
+    out = set()
+    for t in np.linspace(np.log(lo), np.log(hi), count):
+        q = int(round(float(np.exp(t))))
+        q = min(max(q, lo), hi)
+        while q >= 2 and not is_prime(q):
+            q -= 1
+        if q >= 2:
+            out.add(q)
+    return sorted(out)
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def run_cpu_sweep(args):
+    """Times each host representation of libgfpsweep on 512-long vectors (one
+    thread) for primes spread over its domain, as the paper's Figures 5-8 do
+    on older CPUs; prints one JSON line (Mop/s = million multiply-adds/s)."""
+    import platform
+
+    from paper_cs_0404008_gb300 import sweep
+    rank, _, _ = dist_env()
+    if rank != 0:
+        return
+    p32 = sorted(set(sweep_primes(3, 65521, args.sweep_points)) | set(SWEEP_PAPER_PRIMES_32))
+    p64 = sorted(set(sweep_primes(3, 4294967291, args.sweep_points)) | set(SWEEP_PAPER_PRIMES_64))
+    results, residues = {}, {}
+    t_start = time.perf_counter()
+    for v in sweep.VARIANTS:
+        rows = []
+        for p in (p32 if v in sweep.WORD32 else p64):
+            if not sweep.supported(v, p):
+                continue
+            x = gi.uniform(p, SWEEP_N, SWEEP_SEED, 0)
+            y = gi.uniform(p, SWEEP_N, SWEEP_SEED, 1)
+            sec, r = sweep.time(v, p, x, y, 200)
+            reps = max(200, int(200 * 2e-3 / max(sec, 1e-9)))   # about 2 ms per trial
+            best = min(sweep.time(v, p, x, y, reps)[0] for _ in range(3))
+            rows.append([p, round(SWEEP_N * reps / best / 1e6, 1)])
+            residues.setdefault(p, set()).add(r)
+        results[v] = rows
+    consistent = all(len(s) == 1 for s in residues.values())
+    line = {"metric": "host dot-product representation sweep (paper Section 3, Figures 5-8)",
+            "unit": "Mop/s (million multiply-adds per second)", "n": SWEEP_N, "threads": 1,
+            "host": platform.machine(), "cpu": cpu_model(), "data": "synthetic",
+            "inputs": "uint32 residues uniform in [0,p), counter-based generator",
+            "variants_agree": consistent, "seconds": round(time.perf_counter() - t_start, 1),
+            "block_lengths": {v: {str(p): sweep.block(v, p) for p, _ in rows}
+                              for v, rows in results.items()},
+            "results": results}
+    print(json.dumps(line), flush=True)
+    if args.sweep_table:
+        with open(args.sweep_table, "w") as f:
+            for title, fam, ps in (("32-bit words", sweep.WORD32, p32), ("64-bit words and doubles", sweep.WORD64, p64)):
+                f.write(f"### {title} (Mop/s, n = {SWEEP_N}, one thread, {line['host']} {line['cpu']})\n\n")
+                f.write("| p | " + " | ".join(fam) + " |\n|" + "---|" * (len(fam) + 1) + "\n")
+                table = {v: dict((q, m) for q, m in results[v]) for v in fam}
+                for p in ps:
+                    f.write(f"| {p} | " + " | ".join(str(table[v].get(p, "")) for v in fam) + " |\n")
+                f.write("\n")
+    if not consistent:
+        sys.exit(1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -823,7 +932,10 @@ def main():
     ap.add_argument("--no-clocks", action="store_true", help="skip the clock-sampling load phase")
     ap.add_argument("--pairs", type=int, default=COUNT, help="batch size (smaller for profiling)")
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "dot", "matvec", "block", "csr", "serve"])
+                    choices=["batched", "dot", "matvec", "block", "csr", "serve", "cpu_sweep"])
+    ap.add_argument("--sweep-points", type=int, default=24,
+                    help="cpu_sweep: log-spaced primes per word size")
+    ap.add_argument("--sweep-table", default=None, help="cpu_sweep: also write a markdown table")
     ap.add_argument("--requests", type=int, default=20000, help="serve: Poisson requests")
     ap.add_argument("--load", type=float, default=0.7, help="serve: arrival rate / capacity")
     ap.add_argument("--block-m", type=int, default=16384, help="block workload rows (profiling)")
@@ -838,6 +950,8 @@ def main():
         run_gpu(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "cpu_sweep":
+        run_cpu_sweep(args)
     else:
         run_secondary(args)
 

@@ -1,9 +1,11 @@
-"""In-tree build of libgfpdot.so for sm_103a (nvcc, no cmake).
+"""In-tree build of libgfpdot.so for sm_103a (nvcc, no cmake), and of the
+host sweep library libgfpsweep.so (plain C, the host compiler).
 
 Each CUDA translation unit under ``csrc/`` is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -lineinfo -O3`` and linked into
-``_build/libgfpdot.so`` beside this file.  The build is skipped when the
-library is newer than every source and header.
+``_build/libgfpdot.so`` beside this file; ``sweep/gfp_sweep.c`` becomes
+``_build/libgfpsweep.so``.  A build is skipped when its library is newer than
+every source and header it depends on.
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgfpdot.so")
+SWEEP_SRC = os.path.join(HERE, "sweep", "gfp_sweep.c")
+SWEEP_LIB = os.path.join(OUT, "libgfpsweep.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -84,6 +88,28 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     return LIB
 
 
+def build_sweep(force: bool = False) -> str:
+    """Compile libgfpsweep.so with the host C compiler (-O2, no -march, so the
+    same source builds on x86-64 and Arm); returns its path."""
+    deps = [SWEEP_SRC, os.path.join(ROOT, "include", "gfpsweep.h"), os.path.abspath(__file__)]
+    if (not force and os.path.exists(SWEEP_LIB)
+            and all(os.path.getmtime(d) <= os.path.getmtime(SWEEP_LIB) for d in deps)):
+        return SWEEP_LIB
+    os.makedirs(OUT, exist_ok=True)
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        raise RuntimeError("no host C compiler found to build libgfpsweep")
+    tmp = SWEEP_LIB + f".{os.getpid()}.tmp"
+    cmd = [cc, "-O2", "-std=c11", "-fPIC", "-shared", "-fvisibility=default", "-I",
+           os.path.join(ROOT, "include"), "-o", tmp, SWEEP_SRC, "-lm"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"host compiler failed for {SWEEP_SRC}:\n{r.stderr}")
+    os.replace(tmp, SWEEP_LIB)
+    return SWEEP_LIB
+
+
 if __name__ == "__main__":
     import sys
     print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build_sweep(force="--force" in sys.argv))

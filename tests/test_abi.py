@@ -53,7 +53,29 @@ def test_no_oracle_in_product():
         if "_build" in dirpath:
             continue
         for f in files:
-            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp", ".c")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "gfp_oracle" not in txt and "liboracle" not in txt, f
+
+
+def sweep_header_symbols():
+    txt = open(os.path.join(ROOT, "include", "gfpsweep.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(gfp_sweep_\w+)\s*\(", txt)))
+
+
+def test_sweep_library_exports_its_header():
+    from paper_cs_0404008_gb300 import build
+    path = build.build_sweep()
+    syms = sweep_header_symbols()
+    assert len(syms) == 5
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert {s for s in exported if s.startswith("gfp_")} == set(syms)
+
+
+def test_gpu_library_does_not_contain_the_sweep(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.lib_path()], capture_output=True,
+                         text=True).stdout
+    assert "gfp_sweep_" not in out
