@@ -70,6 +70,15 @@ def bind(lib):
     lib.oracle_paper_fp_dot.restype = ctypes.c_uint32
     lib.oracle_paper_fp_dot.argtypes = [ctypes.c_uint32, ctypes.c_uint64, _u32p, _u32p,
                                         ctypes.c_uint64]
+    lib.oracle_gfq_add.restype = ctypes.c_uint32
+    lib.oracle_gfq_add.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                   ctypes.c_uint32]
+    lib.oracle_gfq_mul.restype = ctypes.c_uint32
+    lib.oracle_gfq_mul.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _u32p, ctypes.c_uint32,
+                                   ctypes.c_uint32]
+    lib.oracle_gfq_dot.restype = ctypes.c_uint32
+    lib.oracle_gfq_dot.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _u32p, ctypes.c_uint64,
+                                   _u32p, _u32p]
     return lib
 
 
@@ -259,3 +268,74 @@ def paper_fp_dot(p: int, x, y, K: int):
     y = np.ascontiguousarray(y, dtype=np.uint32)
     r = int(_load().oracle_paper_fp_dot(p, x.shape[0], _p32(x), _p32(y), K))
     return None if r == 0xFFFFFFFF else r
+
+
+# ---- finite fields GF(p^k) (Section 2.4: discrete logarithms, extensions) ----
+#
+# Elements are encoded as sum_j c_j p^j (c_j the coefficient of x^j) in
+# GF(p)[x]/(f), f = x^k + f[k-1] x^(k-1) + ... + f[0] monic, given by f[0..k-1].
+
+def _fvec(f, k):
+    f = np.ascontiguousarray(f, dtype=np.uint32)
+    assert f.shape == (k,)
+    return f
+
+
+def gfq_add(p: int, k: int, a: int, b: int) -> int:
+    return int(_load().oracle_gfq_add(p, k, a, b))
+
+
+def gfq_mul(p: int, k: int, f, a: int, b: int) -> int:
+    return int(_load().oracle_gfq_mul(p, k, _p32(_fvec(f, k)), a, b))
+
+
+def gfq_dot(p: int, k: int, f, x, y) -> int:
+    """Field dot product sum_i x_i y_i in GF(p)[x]/(f), term by term."""
+    x = np.ascontiguousarray(x, dtype=np.uint32)
+    y = np.ascontiguousarray(y, dtype=np.uint32)
+    assert x.shape == y.shape
+    return int(_load().oracle_gfq_dot(p, k, _p32(_fvec(f, k)), x.shape[0], _p32(x), _p32(y)))
+
+
+def gfq_pow(p: int, k: int, f, a: int, e: int) -> int:
+    r, b = (1 if k >= 1 else 0), a
+    while e:
+        if e & 1:
+            r = gfq_mul(p, k, f, r, b)
+        b = gfq_mul(p, k, f, b, b)
+        e >>= 1
+    return r
+
+
+def _prime_factors(n: int):
+    out, d = [], 2
+    while d * d <= n:
+        if n % d == 0:
+            out.append(d)
+            while n % d == 0:
+                n //= d
+        d += 1
+    if n > 1:
+        out.append(n)
+    return out
+
+
+def gfq_x_is_primitive(p: int, k: int, f) -> bool:
+    """True when x generates the multiplicative group of GF(p)[x]/(f) (so the
+    quotient is a field and f is a primitive polynomial)."""
+    q = p ** k
+    x = p if k > 1 else (p - int(f[0])) % p   # the class of x: for k = 1, x = -f[0]
+    if gfq_pow(p, k, f, x, q - 1) != 1:
+        return False
+    return all(gfq_pow(p, k, f, x, (q - 1) // r) != 1 for r in _prime_factors(q - 1))
+
+
+def gfq_find_primitive(p: int, k: int):
+    """The first f (lexicographic in f[0..k-1], f[0] != 0) with x primitive."""
+    import itertools
+    for tail in itertools.product(range(p), repeat=k - 1):
+        for f0 in range(1, p):
+            f = [f0, *tail]
+            if gfq_x_is_primitive(p, k, f):
+                return np.array(f, dtype=np.uint32)
+    raise ValueError(f"no primitive polynomial of degree {k} over GF({p})")

@@ -28,9 +28,13 @@
  * functions so that tests can check them against the plain definition; they
  * are written from the descriptions, with bounds from Eq. (1) and Eq. (2).
  *
+ * Finite fields GF(p^k) (Section 2.4: the discrete-logarithm representation
+ * and field extensions): field addition, multiplication and the term-by-term
+ * field dot product in GF(p)[x]/(f), at the end of this file.
+ *
  * Parity status: every function here is pinned by tests against arbitrary
- * precision brute force, closed forms and invariants (no function is
- * "parity unpinned").
+ * precision brute force, closed forms, invariants and, for GF(2^8), the
+ * worked examples published in FIPS 197 (no function is "parity unpinned").
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -190,4 +194,71 @@ uint32_t oracle_paper_fp_dot(uint32_t p, uint64_t n, const uint32_t *a, const ui
         --left;
     }
     return (uint32_t)oracle_paper_fp_reduce(acc, P);
+}
+
+/*
+ * Finite fields GF(q), q = p^k, for the discrete-logarithm (Zech) dot product
+ * of Section 2.4 ("Discrete logarithms" and "Field extensions").  Plain
+ * definition: an element is a polynomial of degree < k over GF(p), encoded as
+ * the integer sum_j c_j p^j (c_j in [0, p) the coefficient of x^j); the field
+ * is GF(p)[x] / (f) for a monic f = x^k + f_{k-1} x^{k-1} + ... + f_0 given
+ * by its low coefficients f[0..k-1].  Addition adds coefficients mod p;
+ * multiplication is the schoolbook product reduced by x^k = -(f_{k-1} x^{k-1}
+ * + ... + f_0).  The dot product applies these field operations term by term.
+ * For k = 1 (f = x + f_0) the encoding is the residue itself and the
+ * operations are those of GF(p).
+ */
+#define ORACLE_GFQ_MAXK 32
+
+static void gfq_digits(uint32_t p, uint32_t k, uint32_t v, uint32_t *c)
+{
+    for (uint32_t j = 0; j < k; ++j) {
+        c[j] = v % p;
+        v /= p;
+    }
+}
+
+static uint32_t gfq_value(uint32_t p, uint32_t k, const uint32_t *c)
+{
+    uint32_t v = 0;
+    for (uint32_t j = k; j-- > 0;) v = v * p + c[j];
+    return v;
+}
+
+uint32_t oracle_gfq_add(uint32_t p, uint32_t k, uint32_t a, uint32_t b)
+{
+    uint32_t ca[ORACLE_GFQ_MAXK], cb[ORACLE_GFQ_MAXK];
+    gfq_digits(p, k, a, ca);
+    gfq_digits(p, k, b, cb);
+    for (uint32_t j = 0; j < k; ++j) ca[j] = (uint32_t)(((uint64_t)ca[j] + cb[j]) % p);
+    return gfq_value(p, k, ca);
+}
+
+uint32_t oracle_gfq_mul(uint32_t p, uint32_t k, const uint32_t *f, uint32_t a, uint32_t b)
+{
+    uint32_t ca[ORACLE_GFQ_MAXK], cb[ORACLE_GFQ_MAXK];
+    uint64_t prod[2 * ORACLE_GFQ_MAXK];
+    gfq_digits(p, k, a, ca);
+    gfq_digits(p, k, b, cb);
+    for (uint32_t m = 0; m < 2 * k; ++m) prod[m] = 0;
+    for (uint32_t i = 0; i < k; ++i)
+        for (uint32_t j = 0; j < k; ++j) prod[i + j] = (prod[i + j] + (uint64_t)ca[i] * cb[j]) % p;
+    /* reduce from the top degree down: t x^m = t x^{m-k} x^k = -t sum_j f_j x^{m-k+j} */
+    for (uint32_t m = 2 * k - 1; m-- > k;) {
+        const uint64_t t = prod[m];
+        prod[m] = 0;
+        for (uint32_t j = 0; j < k; ++j)
+            prod[m - k + j] = (prod[m - k + j] + (uint64_t)(p - f[j] % p) % p * t) % p;
+    }
+    uint32_t c[ORACLE_GFQ_MAXK];
+    for (uint32_t j = 0; j < k; ++j) c[j] = (uint32_t)prod[j];
+    return gfq_value(p, k, c);
+}
+
+uint32_t oracle_gfq_dot(uint32_t p, uint32_t k, const uint32_t *f, uint64_t n, const uint32_t *x,
+                        const uint32_t *y)
+{
+    uint32_t r = 0;
+    for (uint64_t i = 0; i < n; ++i) r = oracle_gfq_add(p, k, r, oracle_gfq_mul(p, k, f, x[i], y[i]));
+    return r;
 }

@@ -2,7 +2,8 @@
 
 Each case plants one mistake in a copy of the oracle source (a dropped term,
 a wrong index, a transposed operand, a missing reduction, a wrong
-correction constant, a row offset slip), builds it, and checks that at least
+correction constant, a row offset slip, a field reduction dropped or with the
+wrong sign, a reversed digit order), builds it, and checks that at least
 one pin fails for it while the unmodified oracle passes them all.  The
 mistakes live only in temporary copies; the oracle itself is never edited."""
 import random
@@ -56,6 +57,16 @@ def pins_pass() -> bool:
                 return False
             if oracle.paper_block_dot(pp, a, b, K, 64) != bigdot(pp, a, b):
                 return False
+        # GF(p^k): the published GF(2^8) products and the GF(9) facts by hand
+        aes = [1, 1, 0, 1, 1, 0, 0, 0]
+        if (oracle.gfq_mul(2, 8, aes, 0x57, 0x83), oracle.gfq_mul(2, 8, aes, 0x57, 0x13)) != (0xC1, 0xFE):
+            return False
+        if oracle.gfq_add(2, 8, 0x57, 0x83) != 0xD4:
+            return False
+        if (oracle.gfq_mul(3, 2, [1, 0], 3, 3), oracle.gfq_mul(3, 2, [1, 0], 4, 4)) != (2, 6):
+            return False
+        if oracle.gfq_dot(3, 2, [1, 0], [3, 4, 5], [3, 4, 0]) != oracle.gfq_add(3, 2, 2, 6):
+            return False
         return True
     except Exception:
         return False
@@ -78,6 +89,14 @@ MUTATIONS = {
                      "r = zpz_axpy(r, val[q], B[(uint64_t)q * 0 + col[q] + j], p);"),
     "block_tail_skipped": ("    for (; i < n; ++i)\n        res = (res + (uint64_t)a[i] * b[i]) & mask;",
                            "    for (; i + 1 < n; ++i)\n        res = (res + (uint64_t)a[i] * b[i]) & mask;"),
+    "gfq_no_reduction": ("for (uint32_t m = 2 * k - 1; m-- > k;) {",
+                         "for (uint32_t m = k; m-- > k;) {"),
+    "gfq_reduction_sign": ("(uint64_t)(p - f[j] % p) % p * t) % p;",
+                           "(uint64_t)(f[j] % p) * t) % p;"),
+    "gfq_digit_order": ("for (uint32_t j = k; j-- > 0;) v = v * p + c[j];",
+                        "for (uint32_t j = 0; j < k; ++j) v = v * p + c[j];"),
+    "gfq_dot_drops_term": ("for (uint64_t i = 0; i < n; ++i) r = oracle_gfq_add(",
+                           "for (uint64_t i = 1; i < n; ++i) r = oracle_gfq_add("),
 }
 
 

@@ -6,6 +6,7 @@ plus the paper's own dot-product variants (Sections 2.3, 3.1-3.3) restated in
 the oracle and checked against the plain definition.
 """
 import itertools
+import os
 import random
 
 import numpy as np
@@ -222,3 +223,110 @@ def test_paper_fp_dot_matches(p):
     for K in {1, 2, kmax}:
         assert oracle.paper_fp_dot(p, x, y, K) == oracle.dot(p, x, y)
     assert oracle.paper_fp_dot(p, x, y, kmax + 1) is None
+
+
+# ---- GF(p^k): the field arithmetic behind the discrete-logarithm dot product ----
+
+AES_F = [1, 1, 0, 1, 1, 0, 0, 0]   # m(x) = x^8 + x^4 + x^3 + x + 1 (low coefficients)
+
+
+def _fips_cases():
+    here = os.path.dirname(os.path.abspath(__file__))
+    for line in open(os.path.join(here, "golden", "fips197_gf256.txt")):
+        line = line.split("#")[0].split()
+        if line:
+            yield line[0], int(line[1], 16), int(line[2], 16), int(line[3], 16)
+
+
+def test_gfq_fips197_examples():
+    cases = list(_fips_cases())
+    assert len(cases) == 7
+    for op, a, b, want in cases:
+        got = oracle.gfq_add(2, 8, a, b) if op == "add" else oracle.gfq_mul(2, 8, AES_F, a, b)
+        assert got == want, (op, hex(a), hex(b), hex(got))
+    # a dot product of two published products: {57}{83} + {57}{13} = c1 xor fe
+    assert oracle.gfq_dot(2, 8, AES_F, [0x57, 0x57], [0x83, 0x13]) == 0xC1 ^ 0xFE
+
+
+def test_gfq_small_fields_by_hand():
+    # GF(4) = GF(2)[x]/(x^2 + x + 1), w = x (value 2): w^2 = w + 1, w (w + 1) = 1, (w + 1)^2 = w
+    f4 = [1, 1]
+    assert oracle.gfq_mul(2, 2, f4, 2, 2) == 3
+    assert oracle.gfq_mul(2, 2, f4, 2, 3) == 1
+    assert oracle.gfq_mul(2, 2, f4, 3, 3) == 2
+    # GF(9) = GF(3)[x]/(x^2 + 1): x^2 = -1 = 2; (1 + x)^2 = 1 + 2x + x^2 = 2x, value 2*3 = 6
+    f9 = [1, 0]
+    assert oracle.gfq_mul(3, 2, f9, 3, 3) == 2
+    assert oracle.gfq_mul(3, 2, f9, 4, 4) == 6
+    # coefficient-wise addition mod p: (2 + 2x) + (1 + 2x) = 0 + x = value 3
+    assert oracle.gfq_add(3, 2, 8, 7) == 3
+
+
+def _field_axioms(p, k, f, triples):
+    q = p ** k
+    mul = lambda a, b: oracle.gfq_mul(p, k, f, a, b)
+    add = lambda a, b: oracle.gfq_add(p, k, a, b)
+    for a, b, c in triples:
+        assert mul(a, b) == mul(b, a) and add(a, b) == add(b, a)
+        assert mul(mul(a, b), c) == mul(a, mul(b, c))
+        assert mul(a, add(b, c)) == add(mul(a, b), mul(a, c))
+    for a in range(q):
+        assert mul(a, 1) == a and add(a, 0) == a and mul(a, 0) == 0
+        if a:
+            assert any(mul(a, b) == 1 for b in range(1, q)), (p, k, a)
+
+
+def test_gfq_field_axioms_brute_force():
+    import itertools
+    for p, k, f in ((2, 3, [1, 1, 0]), (3, 2, [1, 0]), (2, 2, [1, 1])):
+        q = p ** k
+        _field_axioms(p, k, f, itertools.product(range(q), repeat=3))
+    rng = np.random.default_rng(7)
+    for p, k in ((5, 2), (3, 3), (7, 2), (2, 8)):
+        f = oracle.gfq_find_primitive(p, k)
+        _field_axioms(p, k, f, rng.integers(0, p ** k, (300, 3)).tolist())
+
+
+def test_gfq_frobenius_and_primitive_powers():
+    for p, k in ((2, 3), (3, 2), (5, 2), (2, 8), (3, 5)):
+        f = oracle.gfq_find_primitive(p, k)
+        q = p ** k
+        fr = lambda a: oracle.gfq_pow(p, k, f, a, p)
+        for a in range(min(q, 60)):
+            for b in range(0, min(q, 60), 7):
+                assert fr(oracle.gfq_add(p, k, a, b)) == oracle.gfq_add(p, k, fr(a), fr(b))
+        # x primitive: its q - 1 powers are the q - 1 distinct non-zero elements
+        x = p
+        seen, e = set(), 1
+        for _ in range(q - 1):
+            seen.add(e)
+            e = oracle.gfq_mul(p, k, f, e, x)
+        assert e == 1 and len(seen) == q - 1 and 0 not in seen
+
+
+def test_gfq_prime_field_reduces_to_zpz():
+    """k = 1: GF(p)[x]/(x + f0) is GF(p) itself; the field dot product equals
+    the (separately pinned) Zpz dot product of the residues."""
+    for p in (3, 251, 65521, 65537):
+        x = gi.uniform(p, 700, 11, 0)
+        y = gi.uniform(p, 700, 11, 1)
+        f = oracle.gfq_find_primitive(p, 1)
+        assert oracle.gfq_dot(p, 1, f, x, y) == oracle.dot(p, x, y)
+    # primitivity of x = g in GF(65521) (f = x - g) agrees with Python's modular
+    # powers: g is primitive iff g^((p-1)/r) != 1 for each prime r of p - 1
+    p = 65521
+    for g in range(2, 40):
+        py = all(pow(g, (p - 1) // r, p) != 1 for r in (2, 3, 5, 7, 13))
+        assert oracle.gfq_x_is_primitive(p, 1, [p - g]) == py, g
+
+
+def test_gfq_dot_bilinear():
+    p, k = 3, 5
+    f = oracle.gfq_find_primitive(p, k)
+    q = p ** k
+    rng = np.random.default_rng(3)
+    x, x2, y = (rng.integers(0, q, 200).astype(np.uint32) for _ in range(3))
+    s = np.array([oracle.gfq_add(p, k, int(a), int(b)) for a, b in zip(x, x2)], np.uint32)
+    assert oracle.gfq_dot(p, k, f, s, y) == oracle.gfq_add(p, k, oracle.gfq_dot(p, k, f, x, y),
+                                                          oracle.gfq_dot(p, k, f, x2, y))
+    assert oracle.gfq_dot(p, k, f, x[:0], y[:0]) == 0
