@@ -361,11 +361,11 @@ def run_gpu(args):
         plan._keep = None
         batch.x = batch.y = None
         torch.cuda.empty_cache()
-        for name in ("dot", "matvec", "block", "csr"):
+        for name in ("dot", "matvec", "block", "csr", "gfq"):
             ln = measure_secondary(args, name, g, torch, ctx, stream)
             also[name] = {k: ln[k] for k in ("value", "unit", "ms_per_step", "config", "roofline")
                           if k in ln}
-            for k in ("single_call_us", "graph_of_256_single_dots", "same_gpu"):
+            for k in ("single_call_us", "graph_of_256_single_dots", "same_gpu", "fields"):
                 if k in ln:
                     also[name][k] = ln[k]
             torch.cuda.empty_cache()
@@ -453,12 +453,74 @@ def run_secondary(args):
     print(json.dumps(line), flush=True)
 
 
+GFQ_FIELDS = [(2, 8), (3, 10), (65521, 1)]
+GFQ_N = 1 << 27
+
+
+def measure_gfq(args, g, torch, stream, line, peak, peak_kind):
+    """Discrete-logarithm dot products over GF(2^8), GF(3^10) and GF(65521):
+    2^27 16-bit codes per vector (256 MiB each, larger than L2), one launch per
+    dot product; 4 bytes read per multiply-add."""
+    res = {}
+    n = GFQ_N
+    for p, k in GFQ_FIELDS:
+        q = p ** k
+        f = g.gfp_gfq_find_primitive(p, k)
+        fq = g.Field(p, k, f)
+        v = torch.empty(n, dtype=torch.int32, device="cuda")
+        X = torch.empty(n, dtype=torch.int16, device="cuda")
+        Y = torch.empty(n, dtype=torch.int16, device="cuda")
+        out = torch.empty(8, dtype=torch.int16, device="cuda")
+        seed = gi.BASE_SEED + 7
+        g.gfp_fill_uniform(q, seed, 0, v)
+        fq.to_log(v, X)
+        g.gfp_fill_uniform(q, seed, 1, v)
+        fq.to_log(v, Y)
+        del v
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fq.dot(X, Y, out, n, stream)
+            reps = max(10, args.steps // 10)
+            e0, e1 = _events(torch, 2)
+            e0.record(stream)
+            for _ in range(reps):
+                fq.dot(X, Y, out, n, stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        assert fq.check() == g.GFP_OK
+        t = e0.elapsed_time(e1) / reps
+        gbs = 4.0 * n / (t / 1e3) / 1e9
+        res[f"GF({p}^{k})"] = {"q": q, "ms": t, "gmacs": n / (t / 1e3) / 1e9, "gbs": gbs,
+                               "frac": gbs / peak}
+        fq.close()
+        del X, Y
+        torch.cuda.empty_cache()
+    best = max(res.values(), key=lambda r: r["gmacs"])
+    worst = min(res.values(), key=lambda r: r["gmacs"])
+    line.update({
+        "value": worst["gmacs"], "ms_per_step": worst["ms"],
+        "config": {"workload": "dot products over GF(q) in the discrete-logarithm (Zech) "
+                               "representation, 2^27 uint16 codes per vector, uniform elements, "
+                               "fields GF(2^8), GF(3^10), GF(65521)",
+                   "value_is": "the slowest field"},
+        "roofline": {"bound": "hbm", "achieved": worst["gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": worst["frac"], "kernel": "k_gfq_dot", "traffic": None,
+                     "peak_kind": f"{peak_kind} hbm_gbs", "best_field_frac": best["frac"]},
+        "fields": res,
+        "gpu_launches": 1,
+    })
+    return line
+
+
 def measure_secondary(args, workload, g, torch, ctx, stream):
     """One secondary workload on an existing context; returns its JSON line."""
     peak, peak_kind = hbm_peak()
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic"}
+    if workload == "gfq":
+        return measure_gfq(args, g, torch, stream, line, peak, peak_kind)
     if workload == "dot":
         p, n, nvec = 65521, 1 << 20, 256
         seed = gi.BASE_SEED
@@ -932,7 +994,7 @@ def main():
     ap.add_argument("--no-clocks", action="store_true", help="skip the clock-sampling load phase")
     ap.add_argument("--pairs", type=int, default=COUNT, help="batch size (smaller for profiling)")
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "dot", "matvec", "block", "csr", "serve", "cpu_sweep"])
+                    choices=["batched", "dot", "matvec", "block", "csr", "gfq", "serve", "cpu_sweep"])
     ap.add_argument("--sweep-points", type=int, default=24,
                     help="cpu_sweep: log-spaced primes per word size")
     ap.add_argument("--sweep-table", default=None, help="cpu_sweep: also write a markdown table")

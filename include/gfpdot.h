@@ -401,6 +401,63 @@ GFP_API gfp_status gfp_result_copy(gfp_server *srv, uint64_t ticket, uint32_t *h
 GFP_API gfp_status gfp_release(gfp_server *srv, uint64_t ticket);
 GFP_API gfp_status gfp_server_get_stats(gfp_server *srv, gfp_server_stats *out);
 
+/* ---- finite fields GF(p^k) in the discrete-logarithm representation ---- */
+
+/* Section 2.4 ("Discrete logarithms", "Field extensions"): a dot product over
+ * GF(q), q = p^k <= 2^16, prime field or extension, with every element stored
+ * as a 16-bit code: 0 for zero, e for x^e (1 <= e <= q-2) and q-1 for 1,
+ * where x is the class of x in GF(p)[x]/(f) for a monic f = x^k + f[k-1]
+ * x^(k-1) + ... + f[0] whose powers of x run through all q-1 non-zero
+ * elements (a primitive polynomial).  A product is one code addition modulo
+ * q-1 and a sum one lookup in the table Z[t] = code of 1 + x^t (the paper's
+ * "plus one" table of q entries), so the arithmetic is the same whatever k.
+ *
+ * Element values (the other end of the conversions) encode the polynomial
+ * sum_j c_j x^j (0 <= c_j < p) as the integer sum_j c_j p^j; for k = 1 that is
+ * the residue itself and f = x + f[0] makes x = -f[0] mod p, which must be a
+ * primitive root.
+ *
+ * A field object owns its tables (host-built, resident on `device`) and the
+ * dot product's scratch: dot products and conversions on one field object
+ * must not run concurrently on several streams. */
+typedef struct gfp_gfq gfp_gfq;
+
+/* Writes to f[0..k-1] the first primitive polynomial of degree k over GF(p)
+ * (candidates in lexicographic order of f[k-1..1], then f[0] = 1, 2, ...),
+ * searched on the host.  GFP_ERR_INVALID if p^k > 2^16, p < 2, k < 1, or no
+ * candidate qualifies (p not prime). */
+GFP_API gfp_status gfp_gfq_find_primitive(uint32_t p, uint32_t k, uint32_t *f);
+
+/* Builds GF(p^k) from f[0..k-1] (host array, entries < p) on `device`.
+ * GFP_ERR_INVALID if p^k > 2^16, an entry of f is >= p, or x does not
+ * generate all q-1 non-zero elements modulo f (f reducible or not
+ * primitive, or p not prime); GFP_ERR_NOMEM / GFP_ERR_CUDA on device
+ * failures.  Device memory: 128 KiB table + 8 q bytes + scratch. */
+GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint32_t *f, gfp_gfq **out);
+GFP_API gfp_status gfp_gfq_destroy(gfp_gfq *fq);
+/* p, k and q = p^k of a field (any output pointer may be NULL). */
+GFP_API gfp_status gfp_gfq_info(const gfp_gfq *fq, uint32_t *p, uint32_t *k, uint32_t *q);
+
+/* codes[i] = code of the element values[i] (device arrays, n entries).  A value
+ * >= q yields code 0 and sets the field's error flag (gfp_gfq_check). */
+GFP_API gfp_status gfp_gfq_to_log(gfp_gfq *fq, uint64_t n, const uint32_t *values, uint16_t *codes,
+                                  void *stream);
+/* values[i] = element value of codes[i].  A code > q-1 yields 0 and sets the
+ * error flag. */
+GFP_API gfp_status gfp_gfq_from_log(gfp_gfq *fq, uint64_t n, const uint16_t *codes, uint32_t *values,
+                                    void *stream);
+
+/* *out (device) = code of sum_{i<n} x_i y_i in GF(q), x and y device arrays of
+ * n codes in [0, q-1]; 16-byte aligned x and y take the vectorised path.
+ * n = 0 gives code 0.  Codes above q-1 are outside the contract: the result
+ * is then unspecified (no out-of-bounds access occurs). */
+GFP_API gfp_status gfp_gfq_dot(gfp_gfq *fq, uint64_t n, const uint16_t *x, const uint16_t *y, uint16_t *out,
+                               void *stream);
+
+/* Synchronise the field's device; GFP_ERR_RANGE (and clear the flag) if a
+ * conversion met an out-of-range value or code since the last check. */
+GFP_API gfp_status gfp_gfq_check(gfp_gfq *fq);
+
 /* ---- synthetic inputs (device generator) ---- */
 
 /* out[i] = word(seed, stream_id, offset + i) mod p for 0 <= i < n, where

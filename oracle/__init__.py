@@ -289,12 +289,30 @@ def gfq_mul(p: int, k: int, f, a: int, b: int) -> int:
     return int(_load().oracle_gfq_mul(p, k, _p32(_fvec(f, k)), a, b))
 
 
-def gfq_dot(p: int, k: int, f, x, y) -> int:
-    """Field dot product sum_i x_i y_i in GF(p)[x]/(f), term by term."""
+def gfq_dot(p: int, k: int, f, x, y, threads: int = 1) -> int:
+    """Field dot product sum_i x_i y_i in GF(p)[x]/(f), term by term; with
+    threads > 1 the terms are split into contiguous chunks whose sums are
+    added with the field addition (addition is associative and commutative)."""
     x = np.ascontiguousarray(x, dtype=np.uint32)
     y = np.ascontiguousarray(y, dtype=np.uint32)
     assert x.shape == y.shape
-    return int(_load().oracle_gfq_dot(p, k, _p32(_fvec(f, k)), x.shape[0], _p32(x), _p32(y)))
+    lib = _load()
+    fv = _fvec(f, k)
+    n = x.shape[0]
+    nth = max(1, min(_threads(None) if threads == 0 else threads, n // 4096 or 1))
+    if nth == 1:
+        return int(lib.oracle_gfq_dot(p, k, _p32(fv), n, _p32(x), _p32(y)))
+    edges = np.linspace(0, n, nth + 1).astype(np.int64)
+
+    def run(g):
+        a, b = int(edges[g]), int(edges[g + 1])
+        return int(lib.oracle_gfq_dot(p, k, _p32(fv), b - a, _p32(x[a:b]), _p32(y[a:b])))
+    with ThreadPoolExecutor(nth) as ex:
+        parts = list(ex.map(run, range(nth)))
+    r = 0
+    for v in parts:
+        r = gfq_add(p, k, r, v)
+    return r
 
 
 def gfq_pow(p: int, k: int, f, a: int, e: int) -> int:

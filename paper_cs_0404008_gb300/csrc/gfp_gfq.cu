@@ -1,0 +1,405 @@
+// Dot product over a finite field GF(q), q = p^k <= 2^16, in the discrete-
+// logarithm ("Zech logarithm") representation of Section 2.4, which stays the
+// same for prime fields and their extensions.
+//
+// Codes: the zero element is code 0, the element g^e (g = x, the class of x
+// in GF(p)[x]/(f) for a primitive f) is code e for 1 <= e <= q-2, and 1 = g^0
+// is code q-1 (= qbar).  Hence every non-zero code is congruent to its
+// exponent modulo qbar, and
+//   g^i * g^j = g^(i+j):         code i + j, less qbar when above qbar;
+//   g^i + g^j = g^i (1 + g^(j-i)): code i + Z[(j - i) mod qbar], less qbar when
+//                                 above qbar, where Z[t] is the code of 1 + g^t
+//                                 (Z[t] = 0 when 1 + g^t is zero)
+// with one table Z of qbar entries, as the paper's operation table lays out.
+//
+// The dot-product kernel keeps Z in shared memory (a 64K-entry uint16 table,
+// so every index a masked 16-bit difference can form stays inside it), streams
+// the two code vectors with 16-byte loads, and runs four independent
+// accumulation chains per thread (each addition waits on its table lookup).
+// Warps, then the CTA, combine their partial sums with the same Zech addition;
+// the last CTA to finish (ticket counter) combines the CTA partials.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "gfp_internal.h"
+
+struct gfp_gfq {
+    int device = 0;
+    uint32_t p = 0, k = 0, q = 0, qbar = 0;
+    uint32_t f[16] = {0};
+    uint16_t *d_zech = nullptr;      // 65536 entries; Z[t] for t < qbar, zero beyond
+    uint32_t *d_log = nullptr;       // q entries: element value -> code
+    uint32_t *d_exp = nullptr;       // qbar + 1 entries: code -> element value
+    uint32_t *d_partials = nullptr;  // one per CTA of the dot kernel
+    uint32_t *d_ticket = nullptr;    // finished CTAs (zero outside calls)
+    uint32_t *d_err = nullptr;       // bit 0: a value >= q or a code > qbar was converted
+    int grid = 0;
+};
+
+namespace gfp {
+namespace gfq {
+
+constexpr int THREADS = 1024;
+constexpr uint32_t TABLE = 65536;
+constexpr size_t SMEM = TABLE * sizeof(uint16_t);   // 128 KiB
+
+__device__ __forceinline__ uint32_t zmul(uint32_t a, uint32_t b, uint32_t qbar)
+{
+    uint32_t r = a + b;
+    r = r > qbar ? r - qbar : r;
+    return (a == 0u || b == 0u) ? 0u : r;
+}
+
+// a + c in codes; the table index is masked to 16 bits, so codes outside
+// [0, qbar] (out of contract) give an unspecified code but never leave Z
+__device__ __forceinline__ uint32_t zadd(uint32_t a, uint32_t c, const uint16_t *Z, uint32_t qbar)
+{
+    uint32_t t = c - a;
+    t = c < a ? t + qbar : t;
+    const uint32_t z = Z[t & 0xFFFFu];
+    uint32_t r = a + z;
+    r = r > qbar ? r - qbar : r;
+    r = z == 0u ? 0u : r;
+    r = a == 0u ? c : r;
+    return c == 0u ? a : r;
+}
+
+__device__ __forceinline__ uint32_t warp_zsum(uint32_t v, const uint16_t *Z, uint32_t qbar)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = zadd(v, __shfl_xor_sync(0xffffffffu, v, o), Z, qbar);
+    return v;
+}
+
+__device__ __forceinline__ uint4 ldcs4(const uint16_t *p, uint64_t v)
+{
+    return __ldcs(reinterpret_cast<const uint4 *>(p) + v);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_gfq_dot(const uint16_t *__restrict__ x, const uint16_t *__restrict__ y, uint64_t n,
+              int vec, const uint16_t *__restrict__ Zg, uint32_t qbar, uint32_t *partials,
+              uint32_t *ticket, uint16_t *out)
+{
+    extern __shared__ uint16_t Z[];
+    __shared__ uint32_t wpart[THREADS / 32];
+    __shared__ uint32_t last;
+    // Z[0 .. qbar] is all the arithmetic of valid codes reads
+    const uint32_t nload = (qbar + 8u) / 8u;
+    for (uint32_t i = threadIdx.x; i < nload; i += blockDim.x)
+        reinterpret_cast<uint4 *>(Z)[i] = reinterpret_cast<const uint4 *>(Zg)[i];
+    __syncthreads();
+
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    const uint64_t nvec = vec ? n / 8 : 0;
+    for (uint64_t v = tid; v < nvec; v += nthreads) {
+        const uint4 u = ldcs4(x, v), w = ldcs4(y, v);
+        a0 = zadd(a0, zmul(u.x & 0xFFFFu, w.x & 0xFFFFu, qbar), Z, qbar);
+        a1 = zadd(a1, zmul(u.x >> 16, w.x >> 16, qbar), Z, qbar);
+        a2 = zadd(a2, zmul(u.y & 0xFFFFu, w.y & 0xFFFFu, qbar), Z, qbar);
+        a3 = zadd(a3, zmul(u.y >> 16, w.y >> 16, qbar), Z, qbar);
+        a0 = zadd(a0, zmul(u.z & 0xFFFFu, w.z & 0xFFFFu, qbar), Z, qbar);
+        a1 = zadd(a1, zmul(u.z >> 16, w.z >> 16, qbar), Z, qbar);
+        a2 = zadd(a2, zmul(u.w & 0xFFFFu, w.w & 0xFFFFu, qbar), Z, qbar);
+        a3 = zadd(a3, zmul(u.w >> 16, w.w >> 16, qbar), Z, qbar);
+    }
+    for (uint64_t i = nvec * 8 + tid; i < n; i += nthreads) a0 = zadd(a0, zmul(x[i], y[i], qbar), Z, qbar);
+    uint32_t acc = zadd(zadd(a0, a1, Z, qbar), zadd(a2, a3, Z, qbar), Z, qbar);
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    acc = warp_zsum(acc, Z, qbar);
+    if (lane == 0) wpart[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        acc = lane < (int)(blockDim.x >> 5) ? wpart[lane] : 0u;
+        acc = warp_zsum(acc, Z, qbar);
+        if (lane == 0) {
+            partials[blockIdx.x] = acc;
+            __threadfence();
+            last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    if (last && warp == 0) {
+        __threadfence();
+        acc = 0;
+        for (uint32_t b = lane; b < gridDim.x; b += 32) acc = zadd(acc, __ldcg(partials + b), Z, qbar);
+        acc = warp_zsum(acc, Z, qbar);
+        if (lane == 0) {
+            *out = (uint16_t)acc;
+            *ticket = 0u;   // ready for the next call
+        }
+    }
+}
+
+__global__ void k_gfq_to_log(const uint32_t *__restrict__ v, uint64_t n, const uint32_t *__restrict__ logt,
+                             uint32_t q, uint16_t *__restrict__ codes, uint32_t *err)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = v[i];
+        if (a >= q) {
+            atomicOr(err, 1u);
+            codes[i] = 0;
+        } else {
+            codes[i] = (uint16_t)logt[a];
+        }
+    }
+}
+
+__global__ void k_gfq_from_log(const uint16_t *__restrict__ c, uint64_t n, const uint32_t *__restrict__ expt,
+                               uint32_t qbar, uint32_t *__restrict__ v, uint32_t *err)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = c[i];
+        if (a > qbar) {
+            atomicOr(err, 1u);
+            v[i] = 0;
+        } else {
+            v[i] = expt[a];
+        }
+    }
+}
+
+// ---------------- host: field construction ----------------
+
+// element with base-p digits c[0..k-1] times x, modulo f (x^k = -sum f_j x^j)
+static void times_x(uint32_t p, uint32_t k, const uint32_t *f, uint32_t *c)
+{
+    if (k == 1) {   // x = -f_0
+        c[0] = (uint32_t)((uint64_t)c[0] * ((p - f[0]) % p) % p);
+        return;
+    }
+    const uint64_t t = c[k - 1];
+    for (uint32_t j = k - 1; j >= 1; --j) c[j] = c[j - 1];
+    c[0] = 0;
+    for (uint32_t j = 0; j < k; ++j) c[j] = (uint32_t)((c[j] + (uint64_t)((p - f[j]) % p) * t) % p);
+}
+
+static uint32_t digits_value(uint32_t p, uint32_t k, const uint32_t *c)
+{
+    uint32_t v = 0;
+    for (uint32_t j = k; j-- > 0;) v = v * p + c[j];
+    return v;
+}
+
+// powers of x: expv[e] = value of x^e for e < q-1; false unless x generates
+// all q-1 non-zero elements (so that the quotient ring is a field)
+static bool powers_of_x(uint32_t p, uint32_t k, const uint32_t *f, uint32_t q, std::vector<uint32_t> &expv,
+                        std::vector<uint32_t> &logv)
+{
+    expv.assign(q - 1, 0);
+    logv.assign(q, 0);
+    std::vector<uint8_t> seen(q, 0);
+    uint32_t c[16] = {0};
+    c[0] = 1;
+    for (uint32_t e = 0; e + 1 < q; ++e) {
+        const uint32_t v = digits_value(p, k, c);
+        if (v == 0 || seen[v]) return false;
+        seen[v] = 1;
+        expv[e] = v;
+        logv[v] = e == 0 ? q - 1 : e;
+        times_x(p, k, f, c);
+    }
+    return digits_value(p, k, c) == 1;
+}
+
+static bool order_params(uint32_t p, uint32_t k, uint32_t &q)
+{
+    if (p < 2 || k < 1 || k > 16) return false;
+    uint64_t qq = 1;
+    for (uint32_t i = 0; i < k; ++i) {
+        qq *= p;
+        if (qq > 65536) return false;
+    }
+    q = (uint32_t)qq;
+    return q >= 2;
+}
+
+}  // namespace gfq
+}  // namespace gfp
+
+using namespace gfp;
+
+#define GFQ_TRY(expr)                       \
+    do {                                    \
+        cudaError_t e_ = (expr);            \
+        if (e_ != cudaSuccess) {            \
+            note_cuda_error(e_);            \
+            return GFP_ERR_CUDA;            \
+        }                                   \
+    } while (0)
+
+extern "C" {
+
+GFP_API gfp_status gfp_gfq_find_primitive(uint32_t p, uint32_t k, uint32_t *f)
+{
+    uint32_t q;
+    if (!f || !gfq::order_params(p, k, q)) return GFP_ERR_INVALID;
+    std::vector<uint32_t> expv, logv;
+    std::vector<uint32_t> cand(k, 0);
+    // candidates in lexicographic order of (f[k-1], ..., f[1]), then f[0] = 1 .. p-1
+    for (;;) {
+        for (uint32_t f0 = 1; f0 < p; ++f0) {
+            cand[0] = f0;
+            if (gfq::powers_of_x(p, k, cand.data(), q, expv, logv)) {
+                std::copy(cand.begin(), cand.end(), f);
+                return GFP_OK;
+            }
+        }
+        uint32_t j = 1;
+        while (j < k && ++cand[j] == p) cand[j++] = 0;
+        if (j >= k) return GFP_ERR_INVALID;   // no primitive polynomial: p is not prime
+    }
+}
+
+GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint32_t *f, gfp_gfq **out)
+{
+    uint32_t q;
+    if (!out || !f || !gfq::order_params(p, k, q)) return GFP_ERR_INVALID;
+    *out = nullptr;
+    for (uint32_t j = 0; j < k; ++j)
+        if (f[j] >= p) return GFP_ERR_INVALID;
+    std::vector<uint32_t> expv, logv;
+    if (!gfq::powers_of_x(p, k, f, q, expv, logv)) return GFP_ERR_INVALID;
+    const uint32_t qbar = q - 1;
+    // Z[t] = code of 1 + x^t: add 1 to the constant digit of x^t
+    std::vector<uint16_t> zech(gfq::TABLE, 0);
+    for (uint32_t t = 0; t < qbar; ++t) {
+        uint32_t v = expv[t];
+        const uint32_t d0 = v % p;
+        v = v - d0 + (d0 + 1) % p;
+        zech[t] = (uint16_t)(v == 0 ? 0 : logv[v]);
+    }
+    std::vector<uint32_t> expc(qbar + 1, 0);   // code -> value
+    for (uint32_t c = 1; c <= qbar; ++c) expc[c] = expv[c % qbar];
+
+    int sms = 0;
+    GFQ_TRY(cudaSetDevice(device));
+    GFQ_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    GFQ_TRY(cudaFuncSetAttribute(gfq::k_gfq_dot, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gfq::SMEM));
+    gfp_gfq *fq = new gfp_gfq;
+    fq->device = device;
+    fq->p = p;
+    fq->k = k;
+    fq->q = q;
+    fq->qbar = qbar;
+    for (uint32_t j = 0; j < k; ++j) fq->f[j] = f[j];
+    fq->grid = std::max(1, sms);
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+    };
+    alloc((void **)&fq->d_zech, gfq::SMEM);
+    alloc((void **)&fq->d_log, (size_t)q * 4);
+    alloc((void **)&fq->d_exp, (size_t)(qbar + 1) * 4);
+    alloc((void **)&fq->d_partials, (size_t)fq->grid * 4);
+    alloc((void **)&fq->d_ticket, 4);
+    alloc((void **)&fq->d_err, 4);
+    if (e == cudaSuccess) e = cudaMemcpy(fq->d_zech, zech.data(), gfq::SMEM, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(fq->d_log, logv.data(), (size_t)q * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(fq->d_exp, expc.data(), (size_t)(qbar + 1) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(fq->d_ticket, 0, 4);
+    if (e == cudaSuccess) e = cudaMemset(fq->d_err, 0, 4);
+    if (e != cudaSuccess) {
+        note_cuda_error(e);
+        gfp_gfq_destroy(fq);
+        return e == cudaErrorMemoryAllocation ? GFP_ERR_NOMEM : GFP_ERR_CUDA;
+    }
+    *out = fq;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_gfq_destroy(gfp_gfq *fq)
+{
+    if (!fq) return GFP_ERR_INVALID;
+    cudaSetDevice(fq->device);
+    cudaFree(fq->d_zech);
+    cudaFree(fq->d_log);
+    cudaFree(fq->d_exp);
+    cudaFree(fq->d_partials);
+    cudaFree(fq->d_ticket);
+    cudaFree(fq->d_err);
+    delete fq;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_gfq_info(const gfp_gfq *fq, uint32_t *p, uint32_t *k, uint32_t *q)
+{
+    if (!fq) return GFP_ERR_INVALID;
+    if (p) *p = fq->p;
+    if (k) *k = fq->k;
+    if (q) *q = fq->q;
+    return GFP_OK;
+}
+
+static int conv_grid(const gfp_gfq *fq, uint64_t n)
+{
+    const uint64_t want = (n + 255) / 256;
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)fq->grid * 8));
+}
+
+GFP_API gfp_status gfp_gfq_to_log(gfp_gfq *fq, uint64_t n, const uint32_t *values, uint16_t *codes,
+                                  void *stream)
+{
+    if (!fq || (n && (!values || !codes))) return GFP_ERR_INVALID;
+    if (n == 0) return GFP_OK;
+    GFQ_TRY(cudaSetDevice(fq->device));
+    gfq::k_gfq_to_log<<<conv_grid(fq, n), 256, 0, (cudaStream_t)stream>>>(values, n, fq->d_log, fq->q,
+                                                                          codes, fq->d_err);
+    GFQ_TRY(cudaGetLastError());
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_gfq_from_log(gfp_gfq *fq, uint64_t n, const uint16_t *codes, uint32_t *values,
+                                    void *stream)
+{
+    if (!fq || (n && (!values || !codes))) return GFP_ERR_INVALID;
+    if (n == 0) return GFP_OK;
+    GFQ_TRY(cudaSetDevice(fq->device));
+    gfq::k_gfq_from_log<<<conv_grid(fq, n), 256, 0, (cudaStream_t)stream>>>(codes, n, fq->d_exp, fq->qbar,
+                                                                            values, fq->d_err);
+    GFQ_TRY(cudaGetLastError());
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_gfq_dot(gfp_gfq *fq, uint64_t n, const uint16_t *x, const uint16_t *y, uint16_t *out,
+                               void *stream)
+{
+    if (!fq || !out || (n && (!x || !y))) return GFP_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    GFQ_TRY(cudaSetDevice(fq->device));
+    if (n == 0) {
+        GFQ_TRY(cudaMemsetAsync(out, 0, sizeof(uint16_t), s));
+        return GFP_OK;
+    }
+    const int vec = ((((uintptr_t)x) | ((uintptr_t)y)) & 15u) == 0 ? 1 : 0;
+    const uint64_t work = vec ? (n + 7) / 8 : n;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)fq->grid,
+                                                                    (work + gfq::THREADS - 1) / gfq::THREADS));
+    gfq::k_gfq_dot<<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_zech, fq->qbar, fq->d_partials,
+                                                          fq->d_ticket, out);
+    GFQ_TRY(cudaGetLastError());
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_gfq_check(gfp_gfq *fq)
+{
+    if (!fq) return GFP_ERR_INVALID;
+    GFQ_TRY(cudaSetDevice(fq->device));
+    GFQ_TRY(cudaDeviceSynchronize());
+    uint32_t err = 0;
+    GFQ_TRY(cudaMemcpy(&err, fq->d_err, 4, cudaMemcpyDeviceToHost));
+    if (err) {
+        GFQ_TRY(cudaMemset(fq->d_err, 0, 4));
+        return GFP_ERR_RANGE;
+    }
+    return GFP_OK;
+}
+
+}  // extern "C"

@@ -38,6 +38,9 @@ struct DevUnit {
     uint32_t pad;
 };
 
+// Records a CUDA error for gfp_last_cuda_error (entry points in other units).
+void note_cuda_error(cudaError_t e);
+
 Mod make_mod(uint32_t p);
 uint64_t delay_bound(uint32_t p, int acc_bits, int carried);
 uint64_t k_for(Repr r, uint32_t p);

@@ -111,6 +111,8 @@ static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
         }                                                    \
     } while (0)
 
+void gfp::note_cuda_error(cudaError_t e) { g_last_cuda_error = e; }
+
 static inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 static inline uint32_t lg2_floor(uint64_t n)

@@ -125,6 +125,14 @@ _SIGS = {
     "gfp_plan_save": (_int, [_vp, ctypes.c_char_p]),
     "gfp_plan_size": (_u64, [_vp]),
     "gfp_fill_uniform": (_int, [_u32, _u64, _u64, _u64, _u64, _vp, _vp]),
+    "gfp_gfq_find_primitive": (_int, [_u32, _u32, _vp]),
+    "gfp_gfq_create": (_int, [_int, _u32, _u32, _vp, ctypes.POINTER(_vp)]),
+    "gfp_gfq_destroy": (_int, [_vp]),
+    "gfp_gfq_info": (_int, [_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
+    "gfp_gfq_to_log": (_int, [_vp, _u64, _vp, _vp, _vp]),
+    "gfp_gfq_from_log": (_int, [_vp, _u64, _vp, _vp, _vp]),
+    "gfp_gfq_dot": (_int, [_vp, _u64, _vp, _vp, _vp, _vp]),
+    "gfp_gfq_check": (_int, [_vp]),
     "gfp_server_create": (_int, [ctypes.POINTER(gfp_server_cfg), ctypes.POINTER(_vp)]),
     "gfp_server_destroy": (_int, [_vp]),
     "gfp_register_matrix": (_int, [_vp, _u32, _u64, _u64, _vp, _u64, ctypes.POINTER(_u64)]),
@@ -509,6 +517,86 @@ def gfp_fill_uniform(p: int, seed: int, stream_id: int, out, n: int | None = Non
     _check(load().gfp_fill_uniform(p, seed, stream_id, offset, n, _ptr(out), _stream(stream)),
            "gfp_fill_uniform")
     return out
+
+
+# ---- finite fields GF(p^k), discrete-logarithm representation ----
+
+def gfp_gfq_find_primitive(p: int, k: int):
+    import numpy as np
+    f = np.zeros(max(k, 1), np.uint32)
+    _check(load().gfp_gfq_find_primitive(p, k, f.ctypes.data), "gfp_gfq_find_primitive")
+    return f
+
+
+def _check_u16(t, n: int, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype not in (torch.uint16, torch.int16):
+        raise TypeError(f"{name} must be uint16 (or int16 bit-identical), got {t.dtype}")
+    if not t.is_cuda or not t.is_contiguous() or t.numel() < n:
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of >= {n} elements")
+
+
+class Field:
+    """gfp_gfq: GF(p^k) (q <= 2^16) in the discrete-logarithm representation."""
+
+    def __init__(self, p: int, k: int, f, device: int = 0):
+        import numpy as np
+        import torch
+        torch.cuda.init()
+        fv = np.ascontiguousarray(f, dtype=np.uint32)
+        if fv.shape != (k,):
+            raise ValueError("f needs k coefficients f[0..k-1]")
+        h = _vp()
+        _check(load().gfp_gfq_create(device, p, k, fv.ctypes.data, ctypes.byref(h)), "gfp_gfq_create")
+        self.handle = h
+        self.p, self.k, self.q = p, k, p ** k
+
+    def close(self):
+        if self.handle:
+            _check(load().gfp_gfq_destroy(self.handle), "gfp_gfq_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        p, k, q = _u32(), _u32(), _u32()
+        _check(load().gfp_gfq_info(self.handle, ctypes.byref(p), ctypes.byref(k), ctypes.byref(q)),
+               "gfp_gfq_info")
+        return p.value, k.value, q.value
+
+    def to_log(self, values, codes, n: int | None = None, stream=None):
+        n = values.numel() if n is None else n
+        _check_u32(values, n, "values")
+        _check_u16(codes, n, "codes")
+        _check(load().gfp_gfq_to_log(self.handle, n, _ptr(values), _ptr(codes), _stream(stream)),
+               "gfp_gfq_to_log")
+        return codes
+
+    def from_log(self, codes, values, n: int | None = None, stream=None):
+        n = codes.numel() if n is None else n
+        _check_u16(codes, n, "codes")
+        _check_u32(values, n, "values")
+        _check(load().gfp_gfq_from_log(self.handle, n, _ptr(codes), _ptr(values), _stream(stream)),
+               "gfp_gfq_from_log")
+        return values
+
+    def dot(self, x, y, out, n: int | None = None, stream=None):
+        n = x.numel() if n is None else n
+        _check_u16(x, n, "x")
+        _check_u16(y, n, "y")
+        _check_u16(out, 1, "out")
+        _check(load().gfp_gfq_dot(self.handle, n, _ptr(x), _ptr(y), _ptr(out), _stream(stream)),
+               "gfp_gfq_dot")
+        return out
+
+    def check(self) -> int:
+        return int(load().gfp_gfq_check(self.handle))
 
 
 # ---- service ----
