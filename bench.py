@@ -365,7 +365,7 @@ def run_gpu(args):
             ln = measure_secondary(args, name, g, torch, ctx, stream)
             also[name] = {k: ln[k] for k in ("value", "unit", "ms_per_step", "config", "roofline")
                           if k in ln}
-            for k in ("single_call_us", "graph_of_256_single_dots", "same_gpu", "fields"):
+            for k in ("single_call_us", "graph_of_256_single_dots", "same_gpu", "fields", "p_2^31-1"):
                 if k in ln:
                     also[name][k] = ln[k]
             torch.cuda.empty_cache()
@@ -654,6 +654,19 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                                    ("perterm_cuda_core", g.GFP_REPR_PERTERM, 2)):
                 ctx.set_repr(rp)
                 res[name] = timed(lambda: g.gfp_matmul_block(ctx, p, A, B, C, stream), reps)
+            # a word-size prime beyond the digit range: residue passes on the tensor
+            # cores against the CUDA-core kernel, same shape, inputs below 2^31 - 1
+            pl = 2147483647
+            Al = torch.empty((m, k), dtype=torch.int32, device="cuda")
+            Bl = torch.empty((k, nb), dtype=torch.int32, device="cuda")
+            g.gfp_fill_uniform(pl, seed, 4, Al)
+            g.gfp_fill_uniform(pl, seed, 5, Bl)
+            large = {}
+            for name, rp, reps in (("f16tc_residue_passes", g.GFP_REPR_F16TC, max(5, args.steps // 10)),
+                                   ("u64_carry_cuda_core", g.GFP_REPR_U64_CARRY, 3)):
+                ctx.set_repr(rp)
+                large[name] = timed(lambda: g.gfp_matmul_block(ctx, pl, Al, Bl, C, stream), reps)
+            del Al, Bl
             ctx.set_repr(0)
             assert g.gfp_context_check(ctx) == g.GFP_OK
             t = res["f16tc"]
@@ -670,6 +683,7 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                              "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs",
                              "tensor_tflops_fp16": tflops},
                 "same_gpu": {n: {"ms": v, "gmacs": macs / (v / 1e3) / 1e9} for n, v in res.items()},
+                "p_2^31-1": {n: {"ms": v, "gmacs": macs / (v / 1e3) / 1e9} for n, v in large.items()},
                 "gpu_launches": 2,
             })
         else:
@@ -813,6 +827,18 @@ def measure_serve(args, g):
     wall = time.perf_counter() - t_start
     stats1 = srv.stats()
     lat = np.array([(x[4] - x[3]) / 1e6 for x in results])
+    # latency by job kind (and, for block jobs, by whether the tensor-core path applies)
+    by_kind = {}
+    kinds = np.array([r[0] for r in reqs])
+    for kname, kid in (("dot", 0), ("matvec", 1), ("block", 2)):
+        sel = kinds == kid
+        if sel.any():
+            by_kind[kname] = {"count": int(sel.sum()), "p50_ms": float(np.percentile(lat[sel], 50)),
+                              "p99_ms": float(np.percentile(lat[sel], 99)),
+                              "max_ms": float(lat[sel].max())}
+    top = np.argsort(lat)[-max(1, len(lat) // 100):]
+    by_kind["slowest_1pct_kinds"] = {kname: int((kinds[top] == kid).sum())
+                                     for kname, kid in (("dot", 0), ("matvec", 1), ("block", 2))}
     ok = all(x[0] == g.GFP_OK and x[1] == g.GFP_OK for x in results)
     total_macs = sum(macs(r) for r in reqs)
 
@@ -865,7 +891,8 @@ def measure_serve(args, g):
                   "admission_stalls": stats1["admission_stalls"] - stats0["admission_stalls"],
                   "dot_launches": stats1["dot_launches"] - stats0["dot_launches"],
                   "mean_dot_batch": float(np.mean([x[5] for x, r in zip(results, reqs) if r[0] == 0])),
-                  "mem_peak_bytes": stats1["mem_peak"]},
+                  "mem_peak_bytes": stats1["mem_peak"],
+                  "by_kind": by_kind},
         "gpu_launches": stats1["kernel_launches"] - stats0["kernel_launches"],
     }
     return line

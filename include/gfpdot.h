@@ -75,7 +75,8 @@ typedef enum gfp_repr {
                                floating-point reduction of Section 2.3 (p <= 94906266 only) */
     GFP_REPR_F16TC = 5,     /* block product only: centred residues (Section 3.2.2) split into
                                two balanced 8-bit digits, exact fp16 tensor-core products with
-                               fp32 accumulation over chunks of 1024 terms (p <= 65791) */
+                               fp32 accumulation over chunks of 1024 terms (p <= 65791; larger
+                               p through residues modulo primes <= 65791) */
     GFP_REPR_CENTERED = 6,  /* centred representation (Section 3.2.2): signed residues in
                                [-(p-1)/2, (p-1)/2], signed 64-bit accumulator reduced every
                                k terms, k h^2 + (p-1) <= 2^63 - 1 with h = (p-1)/2 */
@@ -257,11 +258,15 @@ GFP_API gfp_status gfp_matvec_sequence(gfp_ctx *ctx, uint32_t p, uint64_t n, con
 /* C[i*ldc + j] = (sum_t A[i*lda + t] * B[t*ldb + j]) mod p, 0 <= i < m,
  * 0 <= j < nb.  A (m x k), B (k x nb), C (m x nb): device, row-major,
  * lda >= k, ldb >= nb, ldc >= nb; C must not overlap A or B.
- * Path: with GFP_REPR_AUTO or GFP_REPR_F16TC and p <= 65791, A 16-byte
- * aligned and lda a multiple of 4, the tensor-core kernel (two launches: B
- * digit split, then the persistent product); otherwise the CUDA-core kernel
- * with the representation the context resolves for (p, k) (forcing F16TC
- * where it is not eligible gives GFP_ERR_UNSUPPORTED).  The tensor-core path
+ * Path: with GFP_REPR_AUTO or GFP_REPR_F16TC, A 16-byte aligned and lda a
+ * multiple of 4, the tensor cores: for p <= 65791 the digit kernel directly
+ * (two launches: B digit split, then the persistent product); for larger p
+ * one such pass per modulus of a residue number system (the L <= 6 largest
+ * primes <= 65791 whose product exceeds k (p-1)^2, each pass reducing the
+ * inputs modulo its prime) and one launch recombining the residues with
+ * Garner's method modulo p.  Otherwise the CUDA-core kernel with the
+ * representation the context resolves for (p, k) (forcing F16TC where the
+ * tensor cores are not eligible gives GFP_ERR_UNSUPPORTED).  The tensor-core path
  * uses the context's workspace (grown on demand, so call once outside stream
  * capture for the largest shape) and must not run concurrently with another
  * block product of the same context.  k == 0 writes zeros. */

@@ -24,6 +24,14 @@
 //   meet in a u32 workspace through atomics and the CTA that completes a
 //   tile (ticket counter) reduces it into C and clears the workspace.
 //
+// Larger moduli on the tensor cores (p > 65791): the exact integer products
+// sum_t A[i][t] B[t][j] are below k (p-1)^2, so they are fixed by their
+// residues modulo a few small primes p' <= 65791 whose product exceeds that
+// bound (a residue number system).  Each pass runs the tensor-core kernel
+// above modulo one p', reducing every input a < 2^32 to a mod p' while it is
+// split into digits; a last kernel recombines the residues with Garner's
+// mixed-radix method and evaluates the integer modulo p.
+//
 // CUDA-core path (any p <= 2^32-1): shared-memory tiled product with the
 // per-thread unreduced accumulators of the dot-product kernels.
 #include <cuda.h>
@@ -32,6 +40,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "gfp_internal.h"
 #include "gfp_tc.cuh"
@@ -98,6 +107,7 @@ struct Args {
     uint32_t *err;            // bit 0: a bounded wait expired
     Mod mod;
     uint64_t off;             // multiple of p >= 2^41 making recombined values non-negative
+    uint32_t pre_magic;       // floor(2^32 / p) for the input reduction of the residue passes
     uint32_t half;            // (p-1)/2
     uint32_t m_tiles, n_tiles, kblocks, chunks;
     uint64_t units;
@@ -210,6 +220,15 @@ __device__ __forceinline__ void load_tile(const uint8_t *slot, int sub, int ct, 
     }
 }
 
+// a mod p for any 32-bit a and p <= 65791: q = floor(a * floor(2^32/p) / 2^32)
+// is floor(a/p) or one less, so one conditional subtraction finishes it
+__device__ __forceinline__ uint32_t reduce_small(uint32_t a, uint32_t p, uint32_t magic)
+{
+    uint32_t r = a - __umulhi(a, magic) * p;
+    return r >= p ? r - p : r;
+}
+
+template <bool PRE>
 __device__ __forceinline__ void store_digits(const Args &a, const ARegs &r, uint8_t *stage, int ct)
 {
     uint8_t *th = stage;                    // high digits
@@ -219,8 +238,15 @@ __device__ __forceinline__ void store_digits(const Args &a, const ARegs &r, uint
         const int q = ct + 256 * i;
         const int row = q >> 4, c4 = q & 15;
         uint32_t h01, l01, h23, l23;
-        split_pair(r.v[i].x, r.v[i].y, a.mod.p, a.half, h01, l01);
-        split_pair(r.v[i].z, r.v[i].w, a.mod.p, a.half, h23, l23);
+        uint4 w = r.v[i];
+        if (PRE) {
+            w.x = reduce_small(w.x, a.mod.p, a.pre_magic);
+            w.y = reduce_small(w.y, a.mod.p, a.pre_magic);
+            w.z = reduce_small(w.z, a.mod.p, a.pre_magic);
+            w.w = reduce_small(w.w, a.mod.p, a.pre_magic);
+        }
+        split_pair(w.x, w.y, a.mod.p, a.half, h01, l01);
+        split_pair(w.z, w.w, a.mod.p, a.half, h23, l23);
         // 128-byte swizzle: 16-byte chunk j of row r sits at chunk j ^ (r & 7)
         const int j = c4 >> 1, halfsel = c4 & 1;
         const uint32_t off = (uint32_t)row * 128u + ((uint32_t)(j ^ (row & 7)) << 4) + (halfsel << 3);
@@ -229,6 +255,7 @@ __device__ __forceinline__ void store_digits(const Args &a, const ARegs &r, uint
     }
 }
 
+template <bool PRE>
 __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__ Args a)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -414,7 +441,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                 asm volatile("bar.sync 2, %0;" ::"n"(CONV_WARPS * 32) : "memory");
 #pragma unroll
                 for (int sub = 0; sub < KBB; ++sub)
-                    if ((uint32_t)sub < nsub) store_digits(a, r[sub], slot + (size_t)sub * A_TILE_BYTES, ct);
+                    if ((uint32_t)sub < nsub) store_digits<PRE>(a, r[sub], slot + (size_t)sub * A_TILE_BYTES, ct);
                 ptx::fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&bars->conv[s]));
@@ -532,7 +559,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
 // fp16 digits in the 128-byte swizzled K-major layout: rows 0..63 hold the
 // high digits of output columns nt*64 + r, rows 64..127 the low digits.
 __global__ void k_block_prep_b(const uint32_t *B, uint64_t ldb, uint64_t k, uint64_t nb, Mod mod,
-                               uint32_t half, uint32_t kblocks, uint8_t *img)
+                               uint32_t half, uint32_t kblocks, int pre, uint8_t *img)
 {
     const uint32_t tile = blockIdx.x;            // nt * kblocks + kb
     const uint32_t nt = tile / kblocks, kb = tile % kblocks;
@@ -545,6 +572,7 @@ __global__ void k_block_prep_b(const uint32_t *B, uint64_t ldb, uint64_t k, uint
         for (int e = 0; e < 8; ++e) {
             const uint64_t gk = (uint64_t)kb * BK + j * 8 + e;
             v[e] = (gk < k && gcol < nb) ? B[gk * ldb + gcol] : 0u;
+            if (pre) v[e] %= mod.p;
         }
         uint4 wh, wl;
         split_pair(v[0], v[1], mod.p, half, wh.x, wl.x);
@@ -554,6 +582,30 @@ __global__ void k_block_prep_b(const uint32_t *B, uint64_t ldb, uint64_t k, uint
         const int rh = col, rl = col + 64;
         *reinterpret_cast<uint4 *>(out + rh * 128 + ((j ^ (rh & 7)) << 4)) = wh;
         *reinterpret_cast<uint4 *>(out + rl * 128 + ((j ^ (rl & 7)) << 4)) = wl;
+    }
+}
+
+// Garner recombination of L residue matrices R[l] (m x nb, dense) into
+// C = X mod p, where X is the unique integer in [0, prod m_l) with X = R[l]
+// mod m_l: mixed-radix digits v_l in [0, m_l), X = v_0 + m_0 (v_1 + m_1 (v_2
+// + ...)), evaluated modulo p from the innermost term out.
+__global__ void k_block_crt(const uint32_t *R, uint64_t m, uint64_t nb, uint32_t *C, uint64_t ldc, RnsConst rc)
+{
+    const uint64_t count = m * nb;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t v[RNS_MAX];
+#pragma unroll
+        for (int l = 0; l < RNS_MAX; ++l) {
+            if (l >= rc.L) break;
+            const uint32_t ml = rc.mod[l];
+            uint64_t t = R[(uint64_t)l * count + e];
+            for (int j = 0; j < l; ++j) t = (t + ml - v[j] % ml) % ml * rc.inv[l][j] % ml;
+            v[l] = (uint32_t)t;
+        }
+        uint64_t acc = v[rc.L - 1] % rc.p;
+        for (int l = rc.L - 2; l >= 0; --l) acc = (acc * rc.mod[l] + v[l]) % rc.p;
+        C[(e / nb) * ldc + e % nb] = (uint32_t)acc;
     }
 }
 
@@ -626,9 +678,62 @@ __global__ void __launch_bounds__(CC_THREADS)
 
 // ---------------- launchers ----------------
 
+bool block_tc_layout_ok(const uint32_t *A, uint64_t lda)
+{
+    return ((((uintptr_t)A) & 15u) == 0) && (lda % 4 == 0);
+}
+
 bool block_tc_eligible(uint32_t p, const uint32_t *A, uint64_t lda)
 {
-    return p >= 2 && p <= BLOCK_TC_MAX_P && ((((uintptr_t)A) & 15u) == 0) && (lda % 4 == 0);
+    return p >= 2 && p <= BLOCK_TC_MAX_P && block_tc_layout_ok(A, lda);
+}
+
+static uint32_t pow_mod_small(uint64_t b, uint64_t e, uint32_t m)
+{
+    uint64_t r = 1 % m;
+    b %= m;
+    while (e) {
+        if (e & 1) r = r * b % m;
+        b = b * b % m;
+        e >>= 1;
+    }
+    return (uint32_t)r;
+}
+
+bool block_rns_plan(uint32_t p, uint64_t k, RnsConst *rc)
+{
+    // the RNS_MAX largest primes not above BLOCK_TC_MAX_P, by trial division
+    static uint32_t primes[RNS_MAX];
+    static bool ready = false;
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        if (!ready) {
+            int found = 0;
+            for (uint32_t c = BLOCK_TC_MAX_P; found < RNS_MAX; --c) {
+                bool prime = c > 1;
+                for (uint32_t d = 2; prime && d * d <= c; ++d) prime = (c % d) != 0;
+                if (prime) primes[found++] = c;
+            }
+            ready = true;
+        }
+    }
+    if (p < 2) return false;
+    // every exact entry sum_t a_t b_t lies in [0, k (p-1)^2]; the moduli's
+    // product must exceed that to fix it
+    const unsigned __int128 bound = (unsigned __int128)k * (uint64_t)(p - 1) * (uint64_t)(p - 1);
+    unsigned __int128 M = 1;
+    int L = 0;
+    while (L < RNS_MAX && M <= bound) M *= primes[L++];
+    if (M <= bound) return false;
+    rc->L = L;
+    rc->p = p;
+    for (int l = 0; l < RNS_MAX; ++l) {
+        rc->mod[l] = l < L ? primes[l] : 1;
+        for (int j = 0; j < RNS_MAX; ++j)
+            rc->inv[l][j] = (l < L && j < l) ? pow_mod_small(primes[j], primes[l] - 2, primes[l]) : 0;
+    }
+    return true;
 }
 
 size_t block_tc_bimg_bytes(uint64_t k, uint64_t nb)
@@ -674,13 +779,16 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 
 cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb, const uint32_t *A,
                             uint64_t lda, const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc,
-                            void *ws, int sm_count, cudaStream_t s, int *launches)
+                            void *ws, int sm_count, cudaStream_t s, int *launches, bool reduce_inputs)
 {
     using namespace blk;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_block_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)SMEM_BYTES);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_block_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -711,6 +819,7 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
     a.units = (uint64_t)a.n_tiles * a.m_tiles * a.chunks;
     const uint64_t two41 = 1ull << 41;
     a.off = (two41 / mod.p + 1) * (uint64_t)mod.p;
+    a.pre_magic = (uint32_t)((1ull << 32) / mod.p);
     uint8_t *w = (uint8_t *)ws;
     size_t o = (size_t)a.n_tiles * a.kblocks * B_TILE_BYTES;
     o = (o + 255) & ~(size_t)255;
@@ -721,12 +830,24 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
     o += ((a.n_tiles * a.m_tiles * 4 + 255) & ~(size_t)255);
     a.err = (uint32_t *)(w + o);
     k_block_prep_b<<<a.n_tiles * a.kblocks, 256, 0, s>>>(B, ldb, k, nb, mod, a.half, a.kblocks,
-                                                         (uint8_t *)a.Bimg);
+                                                         reduce_inputs ? 1 : 0, (uint8_t *)a.Bimg);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint64_t grid = std::min<uint64_t>(a.units, (uint64_t)sm_count);
-    k_block_tc<<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(a);
+    if (reduce_inputs)
+        k_block_tc<true><<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(a);
+    else
+        k_block_tc<false><<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(a);
     *launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_crt(const uint32_t *R, uint64_t m, uint64_t nb, uint32_t *C, uint64_t ldc,
+                             const RnsConst &rc, int sm_count, cudaStream_t s)
+{
+    const uint64_t count = m * nb;
+    const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 8));
+    blk::k_block_crt<<<(unsigned)blocks, 256, 0, s>>>(R, m, nb, C, ldc, rc);
     return cudaGetLastError();
 }
 

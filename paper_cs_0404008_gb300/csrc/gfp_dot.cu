@@ -188,6 +188,16 @@ __global__ void k_fill_uniform(uint32_t p, uint64_t key, uint64_t offset, uint64
         out[i] = (uint32_t)(mix64(key + 0x9E3779B97F4A7C15ull * (offset + i + 1)) % p);
 }
 
+// the same sequence laid out as a rows x cols matrix with leading dimension ld:
+// out[r*ld + c] = word(r*cols + c) mod p
+__global__ void k_fill_uniform_2d(uint32_t p, uint64_t key, uint64_t rows, uint64_t cols, uint64_t ld,
+                                  uint32_t *out)
+{
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x, n = rows * cols;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += T)
+        out[(i / cols) * ld + i % cols] = (uint32_t)(mix64(key + 0x9E3779B97F4A7C15ull * (i + 1)) % p);
+}
+
 __global__ void k_check_range(const uint32_t *v, uint64_t n, uint32_t p, uint32_t *flag)
 {
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
@@ -285,16 +295,31 @@ cudaError_t launch_dot_batched(const DevPair *pairs, const DevPairAux *aux, cons
     return cudaGetLastError();
 }
 
+static uint64_t fill_key(uint64_t seed, uint64_t stream_id)
+{
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (stream_id + 1);
+    z ^= z >> 30; z *= 0xBF58476D1CE4E5B9ull; z ^= z >> 27; z *= 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 cudaError_t launch_fill_uniform(uint32_t p, uint64_t seed, uint64_t stream_id, uint64_t offset,
                                 uint64_t n, uint32_t *out, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (stream_id + 1);
-    z ^= z >> 30; z *= 0xBF58476D1CE4E5B9ull; z ^= z >> 27; z *= 0x94D049BB133111EBull;
-    const uint64_t key = z ^ (z >> 31);
     uint64_t blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
-    k_fill_uniform<<<(unsigned)blocks, 256, 0, s>>>(p, key, offset, n, out);
+    k_fill_uniform<<<(unsigned)blocks, 256, 0, s>>>(p, fill_key(seed, stream_id), offset, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_uniform_2d(uint32_t p, uint64_t seed, uint64_t stream_id, uint64_t rows,
+                                   uint64_t cols, uint64_t ld, uint32_t *out, cudaStream_t s)
+{
+    const uint64_t n = rows * cols;
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_fill_uniform_2d<<<(unsigned)blocks, 256, 0, s>>>(p, fill_key(seed, stream_id), rows, cols, ld, out);
     return cudaGetLastError();
 }
 

@@ -70,6 +70,9 @@ cudaError_t launch_dot_batched(const DevPair *pairs, const DevPairAux *aux, cons
 int dot_batched_grid(int sm_count);
 cudaError_t launch_fill_uniform(uint32_t p, uint64_t seed, uint64_t stream_id, uint64_t offset,
                                 uint64_t n, uint32_t *out, cudaStream_t s);
+// rows x cols of the same sequence (element r*cols + c) at out[r*ld + c]
+cudaError_t launch_fill_uniform_2d(uint32_t p, uint64_t seed, uint64_t stream_id, uint64_t rows,
+                                   uint64_t cols, uint64_t ld, uint32_t *out, cudaStream_t s);
 cudaError_t launch_check_range(const uint32_t *v, uint64_t n, uint32_t p, uint32_t *flag,
                                cudaStream_t s);
 // u non-null: also *sout = (sum_i u_i y_i) mod p, combined through slot/ticket
@@ -83,11 +86,30 @@ cudaError_t launch_matvec(Repr r, const Mod &m, uint64_t k, uint64_t rows, uint6
 // residues to fit two balanced 8-bit digits: (p-1)/2 <= 32895.
 constexpr uint32_t BLOCK_TC_MAX_P = 65791;
 bool block_tc_eligible(uint32_t p, const uint32_t *A, uint64_t lda);
+// A's layout suits the tensor-core kernel (TMA: 16-byte base, rows 16-byte apart)
+bool block_tc_layout_ok(const uint32_t *A, uint64_t lda);
+
+// Residue-number-system constants of a large-p tensor-core block product:
+// moduli mod[0..L-1] (primes <= BLOCK_TC_MAX_P), inv[l][j] = mod[j]^-1 mod
+// mod[l] for j < l, and the target modulus p.
+constexpr int RNS_MAX = 6;
+struct RnsConst {
+    int L;
+    uint32_t p;
+    uint32_t mod[RNS_MAX];
+    uint32_t inv[RNS_MAX][RNS_MAX];
+};
+// Chooses the moduli for k-term sums of products of residues below p; false
+// when RNS_MAX moduli do not cover k (p-1)^2.
+bool block_rns_plan(uint32_t p, uint64_t k, RnsConst *rc);
+cudaError_t launch_block_crt(const uint32_t *R, uint64_t m, uint64_t nb, uint32_t *C, uint64_t ldc,
+                             const RnsConst &rc, int sm_count, cudaStream_t s);
 size_t block_tc_workspace_bytes(uint64_t m, uint64_t k, uint64_t nb);
 size_t block_tc_bimg_bytes(uint64_t k, uint64_t nb);   // the rest must be zero at launch
 cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb, const uint32_t *A,
                             uint64_t lda, const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc,
-                            void *ws, int sm_count, cudaStream_t s, int *launches);
+                            void *ws, int sm_count, cudaStream_t s, int *launches,
+                            bool reduce_inputs = false);
 uint32_t *block_tc_err_flag(void *ws, uint64_t m, uint64_t k, uint64_t nb);
 // Runs the bounded-wait self test; *status_bits gets the device error word.
 cudaError_t wait_selftest(uint64_t limit_ns, cudaStream_t s, uint32_t *status_bits);

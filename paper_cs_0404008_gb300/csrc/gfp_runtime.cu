@@ -752,7 +752,21 @@ GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64
         GFP_CUDA_TRY(cudaMemset2DAsync(C, ldc * 4, 0, nb * 4, m, s));
         return GFP_OK;
     }
-    const bool tc_ok = block_tc_eligible(p, A, lda);
+    // tensor cores: directly for p <= 65791, through residues modulo small
+    // primes (one pass each, then a Garner recombination) above that
+    const bool layout_ok = block_tc_layout_ok(A, lda);
+    RnsConst rc;
+    const bool direct_ok = layout_ok && p <= BLOCK_TC_MAX_P;
+    bool rns_ok = layout_ok && p > BLOCK_TC_MAX_P && block_rns_plan(p, k, &rc);
+    if (rns_ok && ctx->forced == GFP_REPR_AUTO) {
+        // the residue passes each stream A once (about 4 TB/s) after two
+        // launches; the CUDA-core kernel pays per multiply-add (about 4.5e12/s
+        // at best): keep the residues only where they are expected to win
+        const double t_rns = rc.L * (25e-6 + 4.0 * (double)m * (double)k / 4.0e12);
+        const double t_cc = (double)m * (double)k * (double)nb / 4.5e12;
+        if (t_cc <= t_rns) rns_ok = false;
+    }
+    const bool tc_ok = direct_ok || rns_ok;
     bool use_tc = false;
     Repr r = U64_CARRY;
     if (ctx->forced == GFP_REPR_F16TC) {
@@ -775,7 +789,9 @@ GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64
         return GFP_OK;
     }
     std::lock_guard<std::mutex> g(ctx->mu);
-    const size_t need = block_tc_workspace_bytes(m, k, nb);
+    const size_t tc_need = block_tc_workspace_bytes(m, k, nb);
+    const size_t rns_bytes = rns_ok ? (size_t)rc.L * m * nb * 4 : 0;   // residue matrices after it
+    const size_t need = tc_need + rns_bytes;
     if (need > ctx->blk_ws_bytes) {
         GFP_CUDA_TRY(cudaDeviceSynchronize());
         if (ctx->blk_ws) cudaFree(ctx->blk_ws);
@@ -788,14 +804,23 @@ GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64
     if (m != ctx->blk_m || k != ctx->blk_k || nb != ctx->blk_nb) {
         // the partial-sum region moves with the shape: clear it
         const size_t z = block_tc_bimg_bytes(k, nb);
-        GFP_CUDA_TRY(cudaMemsetAsync((uint8_t *)ctx->blk_ws + z, 0, need - z, s));
+        GFP_CUDA_TRY(cudaMemsetAsync((uint8_t *)ctx->blk_ws + z, 0, tc_need - z, s));
         ctx->blk_m = m;
         ctx->blk_k = k;
         ctx->blk_nb = nb;
     }
     int launches = 0;
-    GFP_CUDA_TRY(launch_block_tc(mod, m, k, nb, A, lda, B, ldb, C, ldc, ctx->blk_ws, ctx->sm_count,
-                                 s, &launches));
+    if (!rns_ok) {
+        GFP_CUDA_TRY(launch_block_tc(mod, m, k, nb, A, lda, B, ldb, C, ldc, ctx->blk_ws, ctx->sm_count,
+                                     s, &launches));
+    } else {
+        uint32_t *R = (uint32_t *)((uint8_t *)ctx->blk_ws + tc_need);
+        for (int l = 0; l < rc.L; ++l)
+            GFP_CUDA_TRY(launch_block_tc(make_mod(rc.mod[l]), m, k, nb, A, lda, B, ldb, R + (size_t)l * m * nb,
+                                         nb, ctx->blk_ws, ctx->sm_count, s, &launches, true));
+        GFP_CUDA_TRY(launch_block_crt(R, m, nb, C, ldc, rc, ctx->sm_count, s));
+        ++launches;
+    }
     ctx->launches += launches;
     return GFP_OK;
 }

@@ -87,6 +87,7 @@ struct Matrix {
     uint64_t rows, cols;
     const uint32_t *dev;
     void *owned;
+    uint64_t ld;   // leading dimension (server-generated matrices pad rows to 16 bytes)
 };
 
 enum class State { Queued, Running, Done };
@@ -304,9 +305,9 @@ int32_t gfp_server::launch_one(uint64_t t, Launch &L)
     const uint64_t before = gfp_launch_count(ctx);
     gfp_status stt;
     if (j.kind == GFP_JOB_MATVEC)
-        stt = gfp_matvec(ctx, j.p, M.rows, M.cols, M.dev, M.cols, v, outp, s);
+        stt = gfp_matvec(ctx, j.p, M.rows, M.cols, M.dev, M.ld, v, outp, s);
     else
-        stt = gfp_matmul_block(ctx, j.p, M.rows, M.cols, j.nb, M.dev, M.cols, v, j.nb, outp, j.nb, s);
+        stt = gfp_matmul_block(ctx, j.p, M.rows, M.cols, j.nb, M.dev, M.ld, v, j.nb, outp, j.nb, s);
     st.kernel_launches += gfp_launch_count(ctx) - before;
     return stt;
 }
@@ -562,12 +563,15 @@ GFP_API gfp_status gfp_register_matrix(gfp_server *s, uint32_t p, uint64_t rows,
 {
     if (!s || !handle || p < 2 || rows == 0 || cols == 0) return GFP_ERR_INVALID;
     if (dev && (((uintptr_t)dev) & 3u)) return GFP_ERR_INVALID;
-    Matrix M{p, rows, cols, dev, nullptr};
+    Matrix M{p, rows, cols, dev, nullptr, cols};
     if (!dev && !s->cfg.simulate) {
+        // rows start on 16-byte boundaries so that the tensor-core block
+        // product (which copies A by TMA) can take the matrix
+        M.ld = (cols + 3) / 4 * 4;
         void *mem = nullptr;
         if (cudaSetDevice(s->cfg.device) != cudaSuccess) return GFP_ERR_CUDA;
-        if (cudaMalloc(&mem, 4 * rows * cols) != cudaSuccess) return GFP_ERR_NOMEM;
-        if (gfp_fill_uniform(p, seed, 0, 0, rows * cols, (uint32_t *)mem, nullptr) != GFP_OK ||
+        if (cudaMalloc(&mem, 4 * rows * M.ld) != cudaSuccess) return GFP_ERR_NOMEM;
+        if (gfp::launch_fill_uniform_2d(p, seed, 0, rows, cols, M.ld, (uint32_t *)mem, nullptr) != cudaSuccess ||
             cudaDeviceSynchronize() != cudaSuccess) {
             cudaFree(mem);
             return GFP_ERR_CUDA;

@@ -93,6 +93,7 @@ def test_block_auto_path_and_unsupported(lib, fresh):
     B = gi.uniform(p, 70 * 9, 63, 1).reshape(70, 9)
     assert np.array_equal(run_block(lib, fresh, p, A, B), oracle.block(p, A, B))
     fresh.set_repr(lib.GFP_REPR_F16TC)
+    # the tensor cores need A 16-byte aligned with lda a multiple of 4 (k = 70 here)
     with pytest.raises(lib.GfpError) as ei:
         run_block(lib, fresh, 2147483647, A, B)
     assert ei.value.status == lib.GFP_ERR_UNSUPPORTED
@@ -118,6 +119,62 @@ def test_block_k_zero_writes_zeros(lib, fresh):
     lib.gfp_matmul_block(fresh, 65521, A, B, C)
     torch.cuda.synchronize()
     assert (host(C) == 0).all()
+
+
+RNS_PRIMES = [65797, 1000003, 67108859, 2147483647, 4294967291]
+RNS_SHAPES = [(1, 1, 1), (7, 13, 5), (129, 1000, 64), (300, 2049, 70), (64, 4101, 3), (257, 1025, 128)]
+
+
+def _pad4(k):
+    return (k + 3) // 4 * 4
+
+
+@pytest.mark.parametrize("p", RNS_PRIMES)
+def test_block_rns_tensor_core_parity(lib, fresh, p):
+    """p above the direct digit range: residues modulo several primes <= 65791
+    on the tensor cores, recombined modulo p (forced and automatic path)."""
+    for i, (m, k, nb) in enumerate(RNS_SHAPES):
+        A = gi.uniform(p, m * k, 66 + i, 0).reshape(m, k)
+        B = gi.uniform(p, k * nb, 66 + i, 1).reshape(k, nb)
+        want = oracle.block(p, A, B)
+        fresh.set_repr(lib.GFP_REPR_F16TC)
+        assert np.array_equal(run_block(lib, fresh, p, A, B, lda=_pad4(k)), want), (p, m, k, nb)
+        fresh.set_repr(lib.GFP_REPR_AUTO)
+        assert np.array_equal(run_block(lib, fresh, p, A, B, lda=_pad4(k), ldc=nb + 3), want)
+
+
+@pytest.mark.parametrize("p", [67108859, 4294967291])
+def test_block_rns_largest_sums(lib, fresh, p):
+    """Every entry p - 1: each exact sum is k (p-1)^2, the bound the moduli
+    must cover; the result is the closed form k mod p."""
+    fresh.set_repr(lib.GFP_REPR_F16TC)
+    for m, k, nb in ((128, 4096, 64), (200, 20000, 64)):
+        A = np.full((m, k), p - 1, np.uint32)
+        B = np.full((k, nb), p - 1, np.uint32)
+        assert (run_block(lib, fresh, p, A, B) == k % p).all(), (p, k)
+
+
+def test_block_rns_matches_cuda_core_path(lib, fresh):
+    p, m, k, nb = 2147483647, 384, 3000, 64
+    A = gi.uniform(p, m * k, 67, 0).reshape(m, k)
+    B = gi.uniform(p, k * nb, 67, 1).reshape(k, nb)
+    fresh.set_repr(lib.GFP_REPR_F16TC)
+    tc = run_block(lib, fresh, p, A, B, lda=_pad4(k))
+    fresh.set_repr(lib.GFP_REPR_U64_CARRY)
+    cc = run_block(lib, fresh, p, A, B, lda=_pad4(k))
+    assert np.array_equal(tc, cc)
+    assert np.array_equal(tc, oracle.block(p, A, B))
+
+
+def test_block_rns_full_size(lib, fresh):
+    """16384 x 16384 x 64 over GF(2^32 - 5) on the tensor cores (five residue
+    passes), every entry against the oracle."""
+    p, m, k, nb = 4294967291, 16384, 16384, 64
+    seed = gi.BASE_SEED + 8
+    A = gi.uniform(p, m * k, seed, 0).reshape(m, k)
+    B = gi.uniform(p, k * nb, seed, 1).reshape(k, nb)
+    got = run_block(lib, fresh, p, A, B)
+    assert np.array_equal(got, oracle.block(p, A, B))
 
 
 def test_block_many_units_per_cta(lib, fresh):
