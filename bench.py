@@ -343,6 +343,22 @@ def run_gpu(args):
         dt = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": batch.macs * world * e2e_steps / dt / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(2 * 4 * batch.total), "d2h_bytes_per_step": int(4 * count)}
+        # the host link bounds this path: measure one large pinned copy on the
+        # same pinned buffer and report the step's input bytes against it
+        dst = torch.empty(batch.total, dtype=torch.int32, device="cuda")
+        dst.copy_(xh, non_blocking=True)
+        torch.cuda.synchronize()
+        c0, c1 = _events(torch, 2)
+        c0.record()
+        for _ in range(3):
+            dst.copy_(xh, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        link = 3 * 4.0 * batch.total / (c0.elapsed_time(c1) / 1e3) / 1e9
+        step_h2d = 2 * 4.0 * batch.total * e2e_steps / dt / 1e9
+        e2e["link"] = {"h2d_gbs_measured": link, "step_input_gbs": step_h2d, "frac": step_h2d / link,
+                       "note": "pinned host-to-device copy of one input vector, same buffers"}
+        del dst
         # results of the e2e path equal the device path
         torch.cuda.synchronize()
         if not np.array_equal(oh.numpy().view(np.uint32), out.cpu().numpy().view(np.uint32)):
