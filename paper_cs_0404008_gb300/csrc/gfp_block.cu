@@ -13,13 +13,17 @@
 //   accumulators are recombined as hh*2^16 + (hl + lh)*2^8 + ll in int64,
 //   reduced mod p, and summed as residues.  Nothing is approximated.
 //   Roles per CTA (one CTA per SM, persistent over (tile, chunk) units):
-//     warp 0      bulk-copies the pre-split B digit tiles (TMA engine)
+//     warp 0      TMA-loads uint32 A boxes (two 64-deep k-blocks per slot)
+//                 from HBM into a ring of shared-memory slots
 //     warp 1      owns TMEM and issues the MMAs (one thread)
-//     warps 2-9   load A uint32 tiles from HBM, centre and split them into
-//                 the two fp16 digit tiles in 128-byte-swizzled shared memory
-//     warps 10-13 drain the accumulators (tcgen05.ld), recombine, reduce
+//     warp 2      bulk-copies the pre-split B digit tiles (own ring)
+//     warps 3-10  read a landed A box into registers, centre and split it,
+//                 and write the two fp16 digit tiles in place over it
+//                 (128-byte-swizzled, K-major), the same 32 KiB per k-block
+//     warps 11-14 drain the accumulators (tcgen05.ld), recombine, reduce
 //   B's digits are stacked [hi | lo] along N (N = 128 per MMA), so one MMA
-//   per A digit yields both products with that digit.
+//   per A digit yields both products with that digit; the two MMAs of a K
+//   step accumulate into separate TMEM columns (two independent chains).
 //   Units of one output tile may be split over two CTAs; their residue sums
 //   meet in a u32 workspace through atomics and the CTA that completes a
 //   tile (ticket counter) reduces it into C and clears the workspace.
