@@ -119,3 +119,32 @@ def test_small_budget_admission_on_gpu(lib):
         assert stt["admission_stalls"] > 0 and stt["mem_peak"] <= 1 << 21
     finally:
         s.close()
+
+
+def test_large_prime_block_job_on_tensor_cores(lib):
+    """A large-p block job big enough for the residue path (five tensor-core
+    passes and a recombination, 11 launches): the server pads the matrix rows
+    (4099 columns) to 16 bytes so the tensor cores can take it, and the result
+    equals the oracle."""
+    s = lib.Server(device=0, mem_budget=1 << 30, n_streams=2)
+    try:
+        p, r, c, nb = 4294967291, 4096, 4099, 64
+        h = s.register_matrix(p, r, c, seed=950)
+        A = gi.uniform(p, r * c, 950, 0).reshape(r, c)
+        before = s.stats()["kernel_launches"]
+        t = s.submit(lib.GFP_JOB_BLOCK, p, matrix=h, nb=nb, seed=951)
+        st, res = s.wait(t, 60_000_000)
+        assert st == lib.GFP_OK and res.status == lib.GFP_OK
+        out = s.result_copy(t, res.out_elems).reshape(r, nb)
+        s.release(t)
+        assert s.stats()["kernel_launches"] - before >= 11
+        B = gi.uniform(p, c * nb, 951, 0).reshape(c, nb)
+        assert np.array_equal(out, oracle.block(p, A, B))
+        # a matvec on the same padded matrix
+        t = s.submit(lib.GFP_JOB_MATVEC, p, matrix=h, seed=952)
+        st, res = s.wait(t, 60_000_000)
+        assert st == lib.GFP_OK and res.status == lib.GFP_OK
+        assert np.array_equal(s.result_copy(t, r), oracle.matvec(p, A, gi.uniform(p, c, 952, 0)))
+        s.release(t)
+    finally:
+        s.close()
