@@ -443,9 +443,40 @@ def cpu_baseline():
         reps += 1
     dt = time.perf_counter() - t0
     macs = float(lens_s.sum()) * reps
-    return {"value": macs / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+    line = {"value": macs / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"every 4th pair of the batch ({len(sel)} pairs, {lens_s.sum():.3e} MACs) "
                       f"x {reps} repetitions, {dt:.2f} s wall on {cores} threads"}
+    line["context"] = cpu_context(ps_s, lens_s, off, x, y, cores, oracle)
+    return line
+
+
+def cpu_context(ps, lens, off, x, y, cores, oracle):
+    """Context beside the oracle figure, on the same sample: the oracle on one
+    thread, and the paper's delayed division on the CPU (libgfpsweep: 64-bit
+    blocks of Section 3.1, and the block-overflow hybrid of Section 3.4, which
+    needs no remainder inside the loop even for p near 2^32) on all cores."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_cs_0404008_gb300 import sweep
+    macs = float(lens.sum())
+    t0 = time.perf_counter()
+    oracle.dot_batch(ps, lens, off, x, y, threads=1)
+    single = macs / (time.perf_counter() - t0) / 1e9
+    out = {"oracle_1_thread": single, "unit": UNIT}
+    ref = oracle.dot_batch(ps, lens, off, x, y, threads=cores)
+    for v in ("block64", "hybrid64"):
+        def run(j):
+            a, n = int(off[j]), int(lens[j])
+            return sweep.dot(v, int(ps[j]), x[a:a + n], y[a:a + n])
+        with ThreadPoolExecutor(cores) as ex:
+            list(ex.map(run, range(min(64, len(ps)))))   # warm-up
+            t0 = time.perf_counter()
+            got = list(ex.map(run, range(len(ps))))
+            dt = time.perf_counter() - t0
+        if not np.array_equal(np.array(got, np.uint32), ref):
+            raise SystemExit(f"cpu {v} differs from the oracle")
+        out[f"delayed_{v}_{cores}_threads"] = macs / dt / 1e9
+    return out
 
 
 # ---------------------------------------------------------------------------
