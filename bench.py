@@ -388,6 +388,16 @@ def run_gpu(args):
         sv = measure_serve(args, g)
         also["serve"] = {"value": sv["value"], "unit": sv["unit"], "config": sv["config"],
                          **sv["serve"]}
+        # the same service at 50 % and 90 % of its measured capacity (shorter streams)
+        sweep = {}
+        for ld in (0.5, 0.9):
+            a2 = argparse.Namespace(**vars(args))
+            a2.load, a2.requests = ld, min(args.requests, 10000)
+            s2 = measure_serve(a2, g)["serve"]
+            sweep[f"{int(ld * 100)}%"] = {k: s2[k] for k in ("p50_ms", "p99_ms", "achieved_jobs_per_s",
+                                                             "all_ok", "verify_mismatches")}
+            sweep[f"{int(ld * 100)}%"]["requests"] = a2.requests
+        also["serve"]["load_sweep"] = sweep
 
     if rank == 0:
         line = {
@@ -614,6 +624,16 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
         plan = g.BatchPlan(ctx, [(p, X[i], Y[i], n) for i in range(nvec)])
         ms, per = time_plan(torch, plan, out, max(10, args.steps // 10), stream)
         t_batch = ms / len(per)
+        # (iv) the plain per-term kernel (one remainder per term) on the same pairs
+        ctx.set_repr(g.GFP_REPR_PERTERM)
+        plan_pt = g.BatchPlan(ctx, [(p, X[i], Y[i], n) for i in range(nvec)])
+        ctx.set_repr(0)
+        out_pt = torch.empty(nvec, dtype=torch.int32, device="cuda")
+        ms_pt, per_pt = time_plan(torch, plan_pt, out_pt, 5, stream)
+        t_pt = ms_pt / len(per_pt)
+        plan_pt.close()
+        if not torch.equal(out_pt, out):
+            raise SystemExit("per-term and tuned batched dots differ")
         macs = float(nvec * n)
         gm = lambda t_ms: macs / (t_ms / 1e3) / 1e9
         line.update({
@@ -623,6 +643,8 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                        "step": "one persistent batched launch over the 256 pairs"},
             "single_call_us": {"p50": lat[len(lat) // 2], "p10": lat[len(lat) // 10],
                                "p90": lat[(9 * len(lat)) // 10]},
+            "same_gpu": {"perterm_ms": t_pt, "perterm_gmacs": gm(t_pt),
+                         "speedup_over_perterm": t_pt / t_batch},
             "graph_of_256_single_dots": {"ms": t_graph, "gmacs": gm(t_graph),
                                           "gbs": 8 * macs / (t_graph / 1e3) / 1e9},
             "roofline": {"bound": "hbm", "achieved": 8 * macs / (t_batch / 1e3) / 1e9, "peak": peak,
