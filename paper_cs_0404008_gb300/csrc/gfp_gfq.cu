@@ -18,6 +18,15 @@
 // accumulation chains per thread (each addition waits on its table lookup).
 // Warps, then the CTA, combine their partial sums with the same Zech addition;
 // the last CTA to finish (ticket counter) combines the CTA partials.
+//
+// Prime fields and fields of characteristic 2 take a cheaper route to the
+// same sum: a product is still a code addition, but each product is turned
+// back into its element value by one lookup in the code-to-value table and
+// the values are added in the additive representation, as integers for
+// GF(p) (a 64-bit sum of values below 2^16 needs no reduction before 2^48
+// terms) and by XOR for GF(2^k) (coefficient-wise addition mod 2); the total
+// is converted to a code once.  That replaces the Zech addition, the costly
+// step of the representation, by one lookup and one add.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -34,6 +43,9 @@ struct gfp_gfq {
     uint32_t *d_partials = nullptr;  // one per CTA of the dot kernel
     uint32_t *d_ticket = nullptr;    // finished CTAs (zero outside calls)
     uint32_t *d_err = nullptr;       // bit 0: a value >= q or a code > qbar was converted
+    uint16_t *d_exp16 = nullptr;     // 65536 entries: code -> element value (0 beyond qbar)
+    unsigned long long *d_acc = nullptr;   // value-domain sum of the dot kernel (zero outside calls)
+    int mode = 0;                    // 0: Zech additions; 1: integer sum (k = 1); 2: XOR (p = 2)
     int grid = 0;
 };
 
@@ -132,6 +144,87 @@ __global__ void __launch_bounds__(THREADS, 1)
             *out = (uint16_t)acc;
             *ticket = 0u;   // ready for the next call
         }
+    }
+}
+
+// Value-domain dot product for GF(p) (XOR = false: integer sum, reduced mod p
+// once) and GF(2^k) (XOR = true): acc += exp(code(x_i) + code(y_i)).
+template <bool XOR>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_gfq_dot_exp(const uint16_t *__restrict__ x, const uint16_t *__restrict__ y, uint64_t n, int vec,
+                  const uint16_t *__restrict__ Eg, uint32_t qbar, uint32_t p, const uint32_t *__restrict__ logt,
+                  unsigned long long *acc_slot, uint32_t *ticket, uint16_t *out)
+{
+    extern __shared__ uint16_t E[];
+    __shared__ unsigned long long wpart[THREADS / 32];
+    __shared__ uint32_t last;
+    const uint32_t nload = (qbar + 8u) / 8u;   // E[0 .. qbar]
+    for (uint32_t i = threadIdx.x; i < nload; i += blockDim.x)
+        reinterpret_cast<uint4 *>(E)[i] = reinterpret_cast<const uint4 *>(Eg)[i];
+    __syncthreads();
+
+    // value of the product of codes a and b (0 if either is the zero element)
+    auto prod = [&](uint32_t a, uint32_t b) -> uint32_t {
+        uint32_t c = a + b;
+        c = c > qbar ? c - qbar : c;
+        const uint32_t v = E[c & 0xFFFFu];
+        return (a == 0u || b == 0u) ? 0u : v;
+    };
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    unsigned long long s0 = 0, s1 = 0;
+    uint32_t x0 = 0, x1 = 0;
+    const uint64_t nvec = vec ? n / 8 : 0;
+    for (uint64_t v = tid; v < nvec; v += nthreads) {
+        const uint4 u = ldcs4(x, v), w = ldcs4(y, v);
+        const uint32_t a0 = prod(u.x & 0xFFFFu, w.x & 0xFFFFu), a1 = prod(u.x >> 16, w.x >> 16);
+        const uint32_t a2 = prod(u.y & 0xFFFFu, w.y & 0xFFFFu), a3 = prod(u.y >> 16, w.y >> 16);
+        const uint32_t a4 = prod(u.z & 0xFFFFu, w.z & 0xFFFFu), a5 = prod(u.z >> 16, w.z >> 16);
+        const uint32_t a6 = prod(u.w & 0xFFFFu, w.w & 0xFFFFu), a7 = prod(u.w >> 16, w.w >> 16);
+        if (XOR) {
+            x0 ^= a0 ^ a1 ^ a2 ^ a3;
+            x1 ^= a4 ^ a5 ^ a6 ^ a7;
+        } else {
+            s0 += (a0 + a1) + (a2 + a3);   // each below 2^16: the 32-bit partial sums cannot wrap
+            s1 += (a4 + a5) + (a6 + a7);
+        }
+    }
+    for (uint64_t i = nvec * 8 + tid; i < n; i += nthreads) {
+        if (XOR) x0 ^= prod(x[i], y[i]);
+        else s0 += prod(x[i], y[i]);
+    }
+    unsigned long long acc = XOR ? (unsigned long long)(x0 ^ x1) : s0 + s1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, acc, o);
+        acc = XOR ? (acc ^ t) : (acc + t);
+    }
+    if (lane == 0) wpart[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        acc = lane < (int)(blockDim.x >> 5) ? wpart[lane] : 0ull;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long t = __shfl_xor_sync(0xffffffffu, acc, o);
+            acc = XOR ? (acc ^ t) : (acc + t);
+        }
+        if (lane == 0) {
+            if (XOR) atomicXor(reinterpret_cast<unsigned int *>(acc_slot), (unsigned int)acc);
+            else atomicAdd(acc_slot, acc);
+            __threadfence();
+            last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long tot = XOR ? (unsigned long long)__ldcg(reinterpret_cast<const unsigned int *>(acc_slot))
+                                           : __ldcg(acc_slot);
+        const uint32_t val = XOR ? (uint32_t)tot : (uint32_t)(tot % p);
+        *out = (uint16_t)logt[val];
+        *acc_slot = 0ull;   // ready for the next call
+        *ticket = 0u;
     }
 }
 
@@ -277,11 +370,17 @@ GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint
     }
     std::vector<uint32_t> expc(qbar + 1, 0);   // code -> value
     for (uint32_t c = 1; c <= qbar; ++c) expc[c] = expv[c % qbar];
+    std::vector<uint16_t> exp16(gfq::TABLE, 0);   // the same as uint16 (values < q <= 2^16)
+    for (uint32_t c = 1; c <= qbar; ++c) exp16[c] = (uint16_t)expc[c];
 
     int sms = 0;
     GFQ_TRY(cudaSetDevice(device));
     GFQ_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     GFQ_TRY(cudaFuncSetAttribute(gfq::k_gfq_dot, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gfq::SMEM));
+    GFQ_TRY(cudaFuncSetAttribute(gfq::k_gfq_dot_exp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gfq::SMEM));
+    GFQ_TRY(cudaFuncSetAttribute(gfq::k_gfq_dot_exp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)gfq::SMEM));
     gfp_gfq *fq = new gfp_gfq;
     fq->device = device;
@@ -291,6 +390,7 @@ GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint
     fq->qbar = qbar;
     for (uint32_t j = 0; j < k; ++j) fq->f[j] = f[j];
     fq->grid = std::max(1, sms);
+    fq->mode = p == 2 ? 2 : (k == 1 ? 1 : 0);
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void **ptr, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
@@ -301,11 +401,15 @@ GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint
     alloc((void **)&fq->d_partials, (size_t)fq->grid * 4);
     alloc((void **)&fq->d_ticket, 4);
     alloc((void **)&fq->d_err, 4);
+    alloc((void **)&fq->d_exp16, gfq::SMEM);
+    alloc((void **)&fq->d_acc, 8);
     if (e == cudaSuccess) e = cudaMemcpy(fq->d_zech, zech.data(), gfq::SMEM, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(fq->d_log, logv.data(), (size_t)q * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(fq->d_exp, expc.data(), (size_t)(qbar + 1) * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(fq->d_ticket, 0, 4);
     if (e == cudaSuccess) e = cudaMemset(fq->d_err, 0, 4);
+    if (e == cudaSuccess) e = cudaMemcpy(fq->d_exp16, exp16.data(), gfq::SMEM, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(fq->d_acc, 0, 8);
     if (e != cudaSuccess) {
         note_cuda_error(e);
         gfp_gfq_destroy(fq);
@@ -325,6 +429,8 @@ GFP_API gfp_status gfp_gfq_destroy(gfp_gfq *fq)
     cudaFree(fq->d_partials);
     cudaFree(fq->d_ticket);
     cudaFree(fq->d_err);
+    cudaFree(fq->d_exp16);
+    cudaFree(fq->d_acc);
     delete fq;
     return GFP_OK;
 }
@@ -382,8 +488,15 @@ GFP_API gfp_status gfp_gfq_dot(gfp_gfq *fq, uint64_t n, const uint16_t *x, const
     const uint64_t work = vec ? (n + 7) / 8 : n;
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)fq->grid,
                                                                     (work + gfq::THREADS - 1) / gfq::THREADS));
-    gfq::k_gfq_dot<<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_zech, fq->qbar, fq->d_partials,
-                                                          fq->d_ticket, out);
+    if (fq->mode == 1)
+        gfq::k_gfq_dot_exp<false><<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_exp16, fq->qbar, fq->p,
+                                                                         fq->d_log, fq->d_acc, fq->d_ticket, out);
+    else if (fq->mode == 2)
+        gfq::k_gfq_dot_exp<true><<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_exp16, fq->qbar, fq->p,
+                                                                        fq->d_log, fq->d_acc, fq->d_ticket, out);
+    else
+        gfq::k_gfq_dot<<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_zech, fq->qbar, fq->d_partials,
+                                                              fq->d_ticket, out);
     GFQ_TRY(cudaGetLastError());
     return GFP_OK;
 }
