@@ -694,7 +694,7 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
             "gpu_launches": iters,
         })
     elif workload in ("block", "csr"):
-        p, m, k, nb = 65521, args.block_m, 16384, 64
+        p, m, k, nb = (args.block_p if workload == "block" else 65521), args.block_m, 16384, 64
         seed = gi.BASE_SEED + 3
         B = torch.empty((k, nb), dtype=torch.int32, device="cuda")
         g.gfp_fill_uniform(p, seed, 1, B)
@@ -717,44 +717,55 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
         if workload == "block":
             A = torch.empty((m, k), dtype=torch.int32, device="cuda")
             g.gfp_fill_uniform(p, seed, 0, A)
+            passes = rns_passes(p, k)
             res = {}
-            for name, rp, reps in (("f16tc", g.GFP_REPR_F16TC, max(10, args.steps // 4)),
-                                   ("u64_block_cuda_core", g.GFP_REPR_U64_BLOCK, 5),
-                                   ("perterm_cuda_core", g.GFP_REPR_PERTERM, 2)):
+            variants = [("f16tc", g.GFP_REPR_F16TC, max(10, args.steps // 4))]
+            if not args.quick:
+                variants += [("u64_block_cuda_core", g.GFP_REPR_U64_BLOCK, 5),
+                             ("perterm_cuda_core", g.GFP_REPR_PERTERM, 2)]
+            for name, rp, reps in variants:
                 ctx.set_repr(rp)
                 res[name] = timed(lambda: g.gfp_matmul_block(ctx, p, A, B, C, stream), reps)
-            # a word-size prime beyond the digit range: residue passes on the tensor
-            # cores against the CUDA-core kernel, same shape, inputs below 2^31 - 1
-            pl = 2147483647
-            Al = torch.empty((m, k), dtype=torch.int32, device="cuda")
-            Bl = torch.empty((k, nb), dtype=torch.int32, device="cuda")
-            g.gfp_fill_uniform(pl, seed, 4, Al)
-            g.gfp_fill_uniform(pl, seed, 5, Bl)
             large = {}
-            for name, rp, reps in (("f16tc_residue_passes", g.GFP_REPR_F16TC, max(5, args.steps // 10)),
-                                   ("u64_carry_cuda_core", g.GFP_REPR_U64_CARRY, 3)):
-                ctx.set_repr(rp)
-                large[name] = timed(lambda: g.gfp_matmul_block(ctx, pl, Al, Bl, C, stream), reps)
-            del Al, Bl
+            if not args.quick and p <= 65791:
+                # a word-size prime beyond the digit range: residue passes on the tensor
+                # cores against the CUDA-core kernel, same shape, inputs below 2^31 - 1
+                pl = 2147483647
+                Al = torch.empty((m, k), dtype=torch.int32, device="cuda")
+                Bl = torch.empty((k, nb), dtype=torch.int32, device="cuda")
+                g.gfp_fill_uniform(pl, seed, 4, Al)
+                g.gfp_fill_uniform(pl, seed, 5, Bl)
+                for name, rp, reps in (("f16tc_residue_passes", g.GFP_REPR_F16TC, max(5, args.steps // 10)),
+                                       ("u64_carry_cuda_core", g.GFP_REPR_U64_CARRY, 3)):
+                    ctx.set_repr(rp)
+                    large[name] = timed(lambda: g.gfp_matmul_block(ctx, pl, Al, Bl, C, stream), reps)
+                del Al, Bl
             ctx.set_repr(0)
             assert g.gfp_context_check(ctx) == g.GFP_OK
             t = res["f16tc"]
-            abytes = 4.0 * m * k + 4.0 * k * nb + 4.0 * m * nb
+            # A is read once per residue pass; the residues (4 bytes each) are
+            # written and read back once by the recombination
+            abytes = passes * (4.0 * m * k + 4.0 * k * nb) + 4.0 * m * nb
+            if passes > 1:
+                abytes += 2 * passes * 4.0 * m * nb
             achieved = abytes / (t / 1e3) / 1e9
-            tflops = 4 * 2 * macs / (t / 1e3) / 1e12   # four digit products per multiply-add
+            tflops = passes * 4 * 2 * macs / (t / 1e3) / 1e12   # four digit products per multiply-add
+            path = ("tensor-core path (balanced fp16 digits)" if passes == 1 else
+                    f"tensor-core path through {passes} residue passes (balanced fp16 digits)")
             line.update({
                 "value": macs / (t / 1e3) / 1e9, "ms_per_step": t,
-                "config": {"workload": f"block product over GF(65521): A {m}x{k} times B {k}x{nb}, "
-                                       "uint32 uniform residues, tensor-core path (balanced fp16 digits)",
+                "config": {"workload": f"block product over GF({p}): A {m}x{k} times B {k}x{nb}, "
+                                       f"uint32 uniform residues, {path}",
                            "l2": "A is larger than L2" if m * k * 4 > (129 << 20) else "A fits L2"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "kernel": "k_block_tc (+k_block_prep_b)",
                              "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs",
                              "tensor_tflops_fp16": tflops},
                 "same_gpu": {n: {"ms": v, "gmacs": macs / (v / 1e3) / 1e9} for n, v in res.items()},
-                "p_2^31-1": {n: {"ms": v, "gmacs": macs / (v / 1e3) / 1e9} for n, v in large.items()},
-                "gpu_launches": 2,
+                "gpu_launches": 2 if passes == 1 else 2 * passes + 1,
             })
+            if large:
+                line["p_2^31-1"] = {n: {"ms": v, "gmacs": macs / (v / 1e3) / 1e9} for n, v in large.items()}
         else:
             row_ptr, col, val = gi.csr_pattern(m, k, 0.01, p, seed)
             rp_d = torch.from_numpy(row_ptr.view(np.int32)).cuda()
@@ -998,6 +1009,22 @@ SWEEP_PAPER_PRIMES_32 = [2887, 2897, 2903, 32749, 40009, 40499, 46337, 65521]
 SWEEP_PAPER_PRIMES_64 = [94906249, 2147483647, 3037000493, 4294967291]
 
 
+def rns_passes(p: int, k: int) -> int:
+    """Tensor-core passes of a k-deep block product over GF(p): one for
+    p <= 65791, else the number of largest primes <= 65791 whose product
+    exceeds k (p-1)^2 (the residue moduli the library picks)."""
+    if p <= 65791:
+        return 1
+    bound, prod, count, c = k * (p - 1) ** 2, 1, 0, 65791
+    while prod <= bound:
+        while not is_prime(c):
+            c -= 1
+        prod *= c
+        count += 1
+        c -= 1
+    return count
+
+
 def is_prime(n: int) -> bool:
     """Deterministic Miller-Rabin for n < 3.3e24 (bases 2..41)."""
     if n < 2:
@@ -1118,6 +1145,8 @@ def main():
     ap.add_argument("--requests", type=int, default=20000, help="serve: Poisson requests")
     ap.add_argument("--load", type=float, default=0.7, help="serve: arrival rate / capacity")
     ap.add_argument("--block-m", type=int, default=16384, help="block workload rows (profiling)")
+    ap.add_argument("--block-p", type=int, default=65521,
+                    help="block workload prime; above 65791 the product runs through residue passes")
     ap.add_argument("--mv-n", type=int, default=32768, help="matvec side (profiling)")
     ap.add_argument("--mv-iters", type=int, default=64, help="matvec iterations (profiling)")
     args = ap.parse_args()
