@@ -279,7 +279,8 @@ GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64
  * k x nb dense.  C[i*ldc + j] = (sum_q val[q] * B[col[q]*ldb + j]) mod p for
  * row_ptr[i] <= q < row_ptr[i+1].  All arrays on the device; row_ptr must be
  * non-decreasing with row_ptr[0] = 0 (checked on the device only when
- * validation is enabled, together with col < k and the residues).  One launch. */
+ * validation is enabled, together with col < k and the residues).  One launch;
+ * k == 0 writes zeros. */
 GFP_API gfp_status gfp_matmul_block_csr(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64_t k,
                                         uint64_t nb, const uint32_t *row_ptr, const uint32_t *col,
                                         const uint32_t *val, const uint32_t *B, uint64_t ldb,

@@ -855,6 +855,10 @@ GFP_API gfp_status gfp_matmul_block_csr(gfp_ctx *ctx, uint32_t p, uint64_t m, ui
         if (st == GFP_OK) st = check_range_rows(ctx, B, k, nb, ldb, p, s);
         if (st != GFP_OK) return st;
     }
+    if (k == 0) {   // no column can hold a nonzero: C = 0 (B has no rows to read)
+        GFP_CUDA_TRY(cudaMemset2DAsync(C, ldc * 4, 0, nb * 4, m, s));
+        return GFP_OK;
+    }
     GFP_CUDA_TRY(launch_block_csr(r, make_mod(p), k_for(r, p), m, k, nb, row_ptr, col, val, B, ldb,
                                   C, ldc, ctx->sm_count, s));
     ctx->launches++;

@@ -215,6 +215,99 @@ def test_csr_parity(lib, fresh, repr_):
             assert np.array_equal(host(C), oracle.csr(p, row_ptr, col, val, B)), (p, m, k, nb)
 
 
+def _csr_run(lib, ctx, p, k, row_ptr, col, val, B, ldb=None, ldc=None, Bd=None):
+    m, nb = row_ptr.shape[0] - 1, B.shape[1]
+    one = np.zeros(1, np.uint32)
+    Cfull = torch.full((m, ldc or nb), -1, dtype=torch.int32, device="cuda")
+    C = Cfull[:, :nb]
+    lib.gfp_matmul_block_csr(ctx, p, k, dev(row_ptr), dev(col) if col.size else dev(one),
+                             dev(val) if val.size else dev(one), dev2(B, ldb) if Bd is None else Bd, C)
+    torch.cuda.synchronize()
+    return host(C)
+
+
+@pytest.mark.parametrize("repr_", [0, 2, 3])
+def test_csr_wide_shapes(lib, fresh, repr_):
+    """The 16-byte-gather sparse-row kernel (nb and ldb multiples of 4): several
+    64-column groups with a ragged last group, rows spanning many 32-nonzero
+    chunks with ragged tails, empty rows, padded leading dimensions and a C
+    whose rows are not 16-byte aligned."""
+    fresh.set_repr(repr_)
+    for p in (65521, 4294967291):
+        for m, k, nb, dens, ldb, ldc in ((300, 5000, 128, 0.05, None, None),
+                                         (40, 3000, 132, 0.3, 136, 133),
+                                         (64, 100, 4, 1.0, 8, 5),
+                                         (257, 700, 64, 0.0, None, None),
+                                         (100, 2000, 192, 0.02, 196, None)):
+            row_ptr, col, val = gi.csr_pattern(m, k, dens, p, seed=73)
+            B = gi.uniform(p, k * nb, 73, 5).reshape(k, nb)
+            got = _csr_run(lib, fresh, p, k, row_ptr, col, val, B, ldb, ldc)
+            assert np.array_equal(got, oracle.csr(p, row_ptr, col, val, B)), (p, m, k, nb, ldb, ldc)
+
+
+def test_csr_unaligned_b_takes_the_general_kernel(lib, fresh):
+    """B rows not 16-byte aligned (a view one element into its storage) and
+    an odd leading dimension: the general sparse-row kernel, same results."""
+    p, m, k, nb = 65521, 80, 900, 64
+    row_ptr, col, val = gi.csr_pattern(m, k, 0.1, p, seed=74)
+    B = gi.uniform(p, k * nb, 74, 1).reshape(k, nb)
+    want = oracle.csr(p, row_ptr, col, val, B)
+    store = torch.zeros(k * nb + 1, dtype=torch.int32, device="cuda")
+    store[1:].copy_(torch.from_numpy(B.reshape(-1).view(np.int32)))
+    Bd = store[1:].view(k, nb)
+    assert Bd.data_ptr() % 16 != 0
+    assert np.array_equal(_csr_run(lib, fresh, p, k, row_ptr, col, val, B, Bd=Bd), want)
+    assert np.array_equal(_csr_run(lib, fresh, p, k, row_ptr, col, val, B, ldb=nb + 1), want)
+
+
+@pytest.mark.parametrize("p,lam", [(554000009, 60), (1073741789, 16), (1073741827, 15)])
+def test_csr_rows_around_the_delay_bound(lib, fresh, p, lam):
+    """Blocked representation at moduli with delay bounds of 60, 16 and 15
+    products, rows of 90-130 nonzeros at the largest residues.  The wide
+    kernel adds plain 64-bit sums and reduces them after every floor(lambda/16)
+    chunks of 32 nonzeros (three chunks; every chunk, where a half adds exactly
+    lambda products; below 16 the representation's own accumulators): an
+    accumulator that overflowed would change the residue."""
+    fresh.set_repr(lib.GFP_REPR_U64_BLOCK)
+    k, nb = 400, 64
+    assert lib.gfp_delay_bound(p, 64, 1) == lam
+    rng = np.random.default_rng(75)
+    rows_c, rows_v = [], []
+    for length in range(90, 131):
+        rows_c.append(np.sort(rng.choice(k, size=length, replace=False)).astype(np.uint32))
+        v = np.full(length, p - 1, np.uint32) if length % 2 == 0 else \
+            rng.integers(0, p, size=length, dtype=np.uint64).astype(np.uint32)
+        rows_v.append(v)
+    row_ptr = np.concatenate([[0], np.cumsum([len(c) for c in rows_c])]).astype(np.uint32)
+    col, val = np.concatenate(rows_c), np.concatenate(rows_v)
+    B = np.full((k, nb), p - 1, np.uint32)
+    B[:, nb // 2:] = rng.integers(0, p, size=(k, nb - nb // 2), dtype=np.uint64).astype(np.uint32)
+    got = _csr_run(lib, fresh, p, k, row_ptr, col, val, B)
+    assert np.array_equal(got, oracle.csr(p, row_ptr, col, val, B))
+
+
+def test_csr_k_zero_writes_zeros(lib, fresh):
+    p, m, nb = 65521, 5, 8
+    row_ptr = np.zeros(m + 1, np.uint32)
+    C = torch.full((m, nb), -1, dtype=torch.int32, device="cuda")
+    one = dev(np.zeros(1, np.uint32))
+    B = torch.zeros((0, nb), dtype=torch.int32, device="cuda")
+    lib.gfp_matmul_block_csr(fresh, p, 0, dev(row_ptr), one, one, B, C)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(C), np.zeros((m, nb), np.uint32))
+
+
+def test_csr_full_size_workload(lib, fresh):
+    """The sparse-row workload: CSR A 16384 x 16384 at density 0.01 times B
+    16384 x 64 over GF(65521), every entry against the oracle."""
+    p, m, k, nb = 65521, 16384, 16384, 64
+    seed = gi.BASE_SEED + 3
+    row_ptr, col, val = gi.csr_pattern(m, k, 0.01, p, seed)
+    B = gi.uniform(p, k * nb, seed, 1).reshape(k, nb)
+    got = _csr_run(lib, fresh, p, k, row_ptr, col, val, B)
+    assert np.array_equal(got, oracle.csr(p, row_ptr, col, val, B))
+
+
 def test_csr_validation(lib, fresh):
     p, m, k, nb = 65521, 10, 20, 8
     row_ptr, col, val = gi.csr_pattern(m, k, 0.3, p, seed=72)
