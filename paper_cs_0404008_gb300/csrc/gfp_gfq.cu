@@ -55,6 +55,9 @@ namespace gfq {
 constexpr int THREADS = 1024;
 constexpr uint32_t TABLE = 65536;
 constexpr size_t SMEM = TABLE * sizeof(uint16_t);   // 128 KiB
+// fields from this size on take the Zech kernel with the rare zero branch
+// (a warp of 256 terms then meets a zero element in a few percent of its steps)
+constexpr uint32_t RARE_Q = 4096;
 
 __device__ __forceinline__ uint32_t zmul(uint32_t a, uint32_t b, uint32_t qbar)
 {
@@ -77,6 +80,27 @@ __device__ __forceinline__ uint32_t zadd(uint32_t a, uint32_t c, const uint16_t 
     return c == 0u ? a : r;
 }
 
+// acc + (code a) * (code b), for fields whose zero element is rare: the
+// common case (a, b, acc nonzero, no cancellation) without selects, and every
+// case involving the zero element (an input or the accumulator is zero, or
+// the sum cancels: Z[t] = 0) through the general code on one rarely taken
+// branch.  Codes are 1..qbar for nonzero elements, 0 for zero.
+__device__ __forceinline__ uint32_t zstep(uint32_t acc, uint32_t a, uint32_t b, const uint16_t *Z,
+                                          uint32_t qbar)
+{
+    uint32_t c = a + b;                         // code of the product (a, b >= 1)
+    c = c > qbar ? c - qbar : c;
+    const uint32_t d = c - acc;                 // (c - acc) mod qbar by an unsigned min
+    const uint32_t t = min(d, d + qbar);
+    const uint32_t z = Z[t & 0xFFFFu];
+    uint32_t r = acc + z;
+    r = r > qbar ? r - qbar : r;
+    // a zero factor shows as a zero product (all four are below 2^16); the two
+    // multiplications run on the multiply-add pipe, off the busier integer ALU
+    if (min(a * b, acc * z) == 0u) r = zadd(acc, zmul(a, b, qbar), Z, qbar);
+    return r;
+}
+
 __device__ __forceinline__ uint32_t warp_zsum(uint32_t v, const uint16_t *Z, uint32_t qbar)
 {
 #pragma unroll
@@ -89,6 +113,10 @@ __device__ __forceinline__ uint4 ldcs4(const uint16_t *p, uint64_t v)
     return __ldcs(reinterpret_cast<const uint4 *>(p) + v);
 }
 
+// RARE: zstep (zero elements handled on a rare branch), for large fields;
+// otherwise the select form of zadd(zmul), for small fields where zeros are
+// frequent enough to make the branch diverge.
+template <bool RARE>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gfq_dot(const uint16_t *__restrict__ x, const uint16_t *__restrict__ y, uint64_t n,
               int vec, const uint16_t *__restrict__ Zg, uint32_t qbar, uint32_t *partials,
@@ -109,14 +137,25 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint64_t nvec = vec ? n / 8 : 0;
     for (uint64_t v = tid; v < nvec; v += nthreads) {
         const uint4 u = ldcs4(x, v), w = ldcs4(y, v);
-        a0 = zadd(a0, zmul(u.x & 0xFFFFu, w.x & 0xFFFFu, qbar), Z, qbar);
-        a1 = zadd(a1, zmul(u.x >> 16, w.x >> 16, qbar), Z, qbar);
-        a2 = zadd(a2, zmul(u.y & 0xFFFFu, w.y & 0xFFFFu, qbar), Z, qbar);
-        a3 = zadd(a3, zmul(u.y >> 16, w.y >> 16, qbar), Z, qbar);
-        a0 = zadd(a0, zmul(u.z & 0xFFFFu, w.z & 0xFFFFu, qbar), Z, qbar);
-        a1 = zadd(a1, zmul(u.z >> 16, w.z >> 16, qbar), Z, qbar);
-        a2 = zadd(a2, zmul(u.w & 0xFFFFu, w.w & 0xFFFFu, qbar), Z, qbar);
-        a3 = zadd(a3, zmul(u.w >> 16, w.w >> 16, qbar), Z, qbar);
+        if constexpr (RARE) {
+            a0 = zstep(a0, u.x & 0xFFFFu, w.x & 0xFFFFu, Z, qbar);
+            a1 = zstep(a1, u.x >> 16, w.x >> 16, Z, qbar);
+            a2 = zstep(a2, u.y & 0xFFFFu, w.y & 0xFFFFu, Z, qbar);
+            a3 = zstep(a3, u.y >> 16, w.y >> 16, Z, qbar);
+            a0 = zstep(a0, u.z & 0xFFFFu, w.z & 0xFFFFu, Z, qbar);
+            a1 = zstep(a1, u.z >> 16, w.z >> 16, Z, qbar);
+            a2 = zstep(a2, u.w & 0xFFFFu, w.w & 0xFFFFu, Z, qbar);
+            a3 = zstep(a3, u.w >> 16, w.w >> 16, Z, qbar);
+        } else {
+            a0 = zadd(a0, zmul(u.x & 0xFFFFu, w.x & 0xFFFFu, qbar), Z, qbar);
+            a1 = zadd(a1, zmul(u.x >> 16, w.x >> 16, qbar), Z, qbar);
+            a2 = zadd(a2, zmul(u.y & 0xFFFFu, w.y & 0xFFFFu, qbar), Z, qbar);
+            a3 = zadd(a3, zmul(u.y >> 16, w.y >> 16, qbar), Z, qbar);
+            a0 = zadd(a0, zmul(u.z & 0xFFFFu, w.z & 0xFFFFu, qbar), Z, qbar);
+            a1 = zadd(a1, zmul(u.z >> 16, w.z >> 16, qbar), Z, qbar);
+            a2 = zadd(a2, zmul(u.w & 0xFFFFu, w.w & 0xFFFFu, qbar), Z, qbar);
+            a3 = zadd(a3, zmul(u.w >> 16, w.w >> 16, qbar), Z, qbar);
+        }
     }
     for (uint64_t i = nvec * 8 + tid; i < n; i += nthreads) a0 = zadd(a0, zmul(x[i], y[i], qbar), Z, qbar);
     uint32_t acc = zadd(zadd(a0, a1, Z, qbar), zadd(a2, a3, Z, qbar), Z, qbar);
@@ -376,7 +415,9 @@ GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint
     int sms = 0;
     GFQ_TRY(cudaSetDevice(device));
     GFQ_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-    GFQ_TRY(cudaFuncSetAttribute(gfq::k_gfq_dot, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GFQ_TRY(cudaFuncSetAttribute(gfq::k_gfq_dot<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gfq::SMEM));
+    GFQ_TRY(cudaFuncSetAttribute(gfq::k_gfq_dot<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)gfq::SMEM));
     GFQ_TRY(cudaFuncSetAttribute(gfq::k_gfq_dot_exp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)gfq::SMEM));
@@ -494,9 +535,12 @@ GFP_API gfp_status gfp_gfq_dot(gfp_gfq *fq, uint64_t n, const uint16_t *x, const
     else if (fq->mode == 2)
         gfq::k_gfq_dot_exp<true><<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_exp16, fq->qbar, fq->p,
                                                                         fq->d_log, fq->d_acc, fq->d_ticket, out);
+    else if (fq->q >= gfq::RARE_Q)
+        gfq::k_gfq_dot<true><<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_zech, fq->qbar,
+                                                                    fq->d_partials, fq->d_ticket, out);
     else
-        gfq::k_gfq_dot<<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_zech, fq->qbar, fq->d_partials,
-                                                              fq->d_ticket, out);
+        gfq::k_gfq_dot<false><<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_zech, fq->qbar,
+                                                                     fq->d_partials, fq->d_ticket, out);
     GFQ_TRY(cudaGetLastError());
     return GFP_OK;
 }

@@ -13,7 +13,7 @@ from paper_cs_0404008_gb300 import gfpdot as g
 pytestmark = pytest.mark.gpu
 
 FIELDS = [(2, 1), (3, 1), (2, 8), (3, 2), (5, 3), (17, 3), (13, 4), (251, 1), (65521, 1),
-          (3, 10), (2, 16)]
+          (3, 10), (2, 16), (5, 6), (7, 5)]
 _F = {}
 
 
@@ -114,6 +114,37 @@ def test_products_and_cancellation():
             assert gpu_dot(fq, a, np.zeros(64, np.uint32)) == 0
         finally:
             fq.close()
+
+
+@pytest.mark.parametrize("p,k", [(3, 2), (5, 3), (17, 3), (13, 4), (3, 10), (5, 6), (7, 5)])
+def test_accumulator_chains_cancel_and_restart(p, k):
+    """Codes 8j+i and 8j+i+4 carry v*1 and v*(-1), so each of a thread's four
+    accumulator chains returns to the zero element after every 8-code step
+    and restarts from it: the zero-accumulator and cancellation cases of the
+    Zech step run in every thread, on the small-field and large-field
+    kernels.  One step that does not cancel leaves a nonzero result."""
+    f = field_poly(p, k)
+    q = p ** k
+    fq = g.Field(p, k, f)
+    try:
+        n = 8 * 40000
+        rng = np.random.default_rng(11)
+        v = rng.integers(1, q, size=(n // 8, 4)).astype(np.uint32)
+        x = np.empty((n // 8, 8), np.uint32)
+        y = np.empty((n // 8, 8), np.uint32)
+        x[:, :4] = v
+        x[:, 4:] = v
+        y[:, :4] = 1
+        y[:, 4:] = p - 1          # -1: constant digit p - 1
+        y[123, 4:] = 1            # this step doubles instead (p > 2)
+        x, y = x.reshape(-1), y.reshape(-1)
+        want = oracle.gfq_dot(p, k, f, x, y, threads=16)
+        assert want != 0
+        assert gpu_dot(fq, x, y) == want
+        y[123 * 8 + 4:123 * 8 + 8] = p - 1
+        assert gpu_dot(fq, x, y) == 0
+    finally:
+        fq.close()
 
 
 def test_field_construction_errors():
