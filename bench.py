@@ -196,6 +196,15 @@ def traffic_record(kernel: str):
     return rec
 
 
+def traffic_for(kernel: str, alg_bytes: float):
+    """DRAM bytes of one launch of `kernel` on this line's workload: the
+    committed ncu ratio of DRAM bytes to algorithmic bytes times the line's
+    algorithmic bytes per launch (None when there is no record or the
+    kernel's sources changed since it was taken)."""
+    rec = traffic_record(kernel)
+    return rec["dram_bytes_per_algorithmic_byte"] * alg_bytes if rec else None
+
+
 class Batch:
     """The batched workload generated on the device (same definition as the
     host generator: pair i uses streams 2+2i and 3+2i)."""
@@ -562,7 +571,8 @@ def measure_gfq(args, g, torch, stream, line, peak, peak_kind):
                                "fields GF(2^8), GF(3^10), GF(65521)",
                    "value_is": "the slowest field"},
         "roofline": {"bound": "hbm", "achieved": worst["gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": worst["frac"], "kernel": "k_gfq_dot", "traffic": None,
+                     "frac": worst["frac"], "kernel": "k_gfq_dot",
+                     "traffic": traffic_for("k_gfq_dot", 4.0 * n),
                      "peak_kind": f"{peak_kind} hbm_gbs", "best_field_frac": best["frac"]},
         "fields": res,
         "gpu_launches": 1,
@@ -649,7 +659,8 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                                           "gbs": 8 * macs / (t_graph / 1e3) / 1e9},
             "roofline": {"bound": "hbm", "achieved": 8 * macs / (t_batch / 1e3) / 1e9, "peak": peak,
                          "unit": "GB/s", "frac": 8 * macs / (t_batch / 1e3) / 1e9 / peak,
-                         "kernel": "k_dot_batched", "traffic": None,
+                         "kernel": "k_dot_batched",
+                         "traffic": traffic_for("k_dot_batched", 8 * macs + 4.0 * nvec),
                          "peak_kind": f"{peak_kind} hbm_gbs"},
             "gpu_launches": len(per),
         })
@@ -687,7 +698,8 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                        "l2": "A is 4 GiB, larger than L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "kernel": "k_matvec",
-                         "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs"},
+                         "traffic": traffic_for("k_matvec", 4.0 * n * n + 8.0 * n),
+                         "peak_kind": f"{peak_kind} hbm_gbs"},
             "same_gpu": {"perterm_ms": res["perterm"],
                          "perterm_gmacs": macs / (res["perterm"] / 1e3) / 1e9,
                          "speedup_over_perterm": res["perterm"] / t},
@@ -759,7 +771,8 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                            "l2": "A is larger than L2" if m * k * 4 > (129 << 20) else "A fits L2"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "kernel": "k_block_tc (+k_block_prep_b)",
-                             "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs",
+                             "traffic": traffic_for("k_block_tc", abytes) if passes == 1 else None,
+                             "peak_kind": f"{peak_kind} hbm_gbs",
                              "tensor_tflops_fp16": tflops},
                 "same_gpu": {n: {"ms": v, "gmacs": macs / (v / 1e3) / 1e9} for n, v in res.items()},
                 "gpu_launches": 2 if passes == 1 else 2 * passes + 1,
@@ -798,7 +811,8 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                            "l2": "flushed before each timed product (inputs 26 MB fit L2)"},
                 "roofline": {"bound": "hbm", "achieved": abytes / (t / 1e3) / 1e9, "peak": peak,
                              "unit": "GB/s", "frac": abytes / (t / 1e3) / 1e9 / peak,
-                             "kernel": "k_block_csr", "traffic": None,
+                             "kernel": "k_block_csr_wide",
+                             "traffic": traffic_for("k_block_csr_wide", abytes),
                              "peak_kind": f"{peak_kind} hbm_gbs",
                              "note": "B (4 MiB) is re-read from L2 per nonzero; HBM bytes count it once"},
                 "gpu_launches": 1,
