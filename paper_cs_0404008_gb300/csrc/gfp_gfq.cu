@@ -58,6 +58,13 @@ constexpr size_t SMEM = TABLE * sizeof(uint16_t);   // 128 KiB
 // fields from this size on take the Zech kernel with the rare zero branch
 // (a warp of 256 terms then meets a zero element in a few percent of its steps)
 constexpr uint32_t RARE_Q = 4096;
+// grid strides per loop iteration: with one 1024-thread CTA per SM (the table
+// takes 128 KiB of shared memory) and 64 registers per thread, eight 16-byte
+// loads in flight per thread are what keeps HBM busy (one stride: 0.75-0.77 of
+// the copy bandwidth for the value-domain sums, four: 0.88-0.94)
+#ifndef GFQ_NS
+#define GFQ_NS 4
+#endif
 
 __device__ __forceinline__ uint32_t zmul(uint32_t a, uint32_t b, uint32_t qbar)
 {
@@ -135,8 +142,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
     uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     const uint64_t nvec = vec ? n / 8 : 0;
-    for (uint64_t v = tid; v < nvec; v += nthreads) {
-        const uint4 u = ldcs4(x, v), w = ldcs4(y, v);
+    auto step = [&](const uint4 &u, const uint4 &w) {
         if constexpr (RARE) {
             a0 = zstep(a0, u.x & 0xFFFFu, w.x & 0xFFFFu, Z, qbar);
             a1 = zstep(a1, u.x >> 16, w.x >> 16, Z, qbar);
@@ -156,7 +162,20 @@ __global__ void __launch_bounds__(THREADS, 1)
             a2 = zadd(a2, zmul(u.w & 0xFFFFu, w.w & 0xFFFFu, qbar), Z, qbar);
             a3 = zadd(a3, zmul(u.w >> 16, w.w >> 16, qbar), Z, qbar);
         }
+    };
+    // GFQ_NS strides per iteration: 2 GFQ_NS 16-byte loads in flight per thread
+    uint64_t v = tid;
+    for (; v + (GFQ_NS - 1) * nthreads < nvec; v += GFQ_NS * nthreads) {
+        uint4 u[GFQ_NS], w[GFQ_NS];
+#pragma unroll
+        for (int j = 0; j < GFQ_NS; ++j) {
+            u[j] = ldcs4(x, v + j * nthreads);
+            w[j] = ldcs4(y, v + j * nthreads);
+        }
+#pragma unroll
+        for (int j = 0; j < GFQ_NS; ++j) step(u[j], w[j]);
     }
+    for (; v < nvec; v += nthreads) step(ldcs4(x, v), ldcs4(y, v));
     for (uint64_t i = nvec * 8 + tid; i < n; i += nthreads) a0 = zadd(a0, zmul(x[i], y[i], qbar), Z, qbar);
     uint32_t acc = zadd(zadd(a0, a1, Z, qbar), zadd(a2, a3, Z, qbar), Z, qbar);
 
@@ -214,8 +233,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     unsigned long long s0 = 0, s1 = 0;
     uint32_t x0 = 0, x1 = 0;
     const uint64_t nvec = vec ? n / 8 : 0;
-    for (uint64_t v = tid; v < nvec; v += nthreads) {
-        const uint4 u = ldcs4(x, v), w = ldcs4(y, v);
+    auto step = [&](const uint4 &u, const uint4 &w) {
         const uint32_t a0 = prod(u.x & 0xFFFFu, w.x & 0xFFFFu), a1 = prod(u.x >> 16, w.x >> 16);
         const uint32_t a2 = prod(u.y & 0xFFFFu, w.y & 0xFFFFu), a3 = prod(u.y >> 16, w.y >> 16);
         const uint32_t a4 = prod(u.z & 0xFFFFu, w.z & 0xFFFFu), a5 = prod(u.z >> 16, w.z >> 16);
@@ -227,7 +245,20 @@ __global__ void __launch_bounds__(THREADS, 1)
             s0 += (a0 + a1) + (a2 + a3);   // each below 2^16: the 32-bit partial sums cannot wrap
             s1 += (a4 + a5) + (a6 + a7);
         }
+    };
+    // GFQ_NS strides per iteration: 2 GFQ_NS 16-byte loads in flight per thread
+    uint64_t v = tid;
+    for (; v + (GFQ_NS - 1) * nthreads < nvec; v += GFQ_NS * nthreads) {
+        uint4 u[GFQ_NS], w[GFQ_NS];
+#pragma unroll
+        for (int j = 0; j < GFQ_NS; ++j) {
+            u[j] = ldcs4(x, v + j * nthreads);
+            w[j] = ldcs4(y, v + j * nthreads);
+        }
+#pragma unroll
+        for (int j = 0; j < GFQ_NS; ++j) step(u[j], w[j]);
     }
+    for (; v < nvec; v += nthreads) step(ldcs4(x, v), ldcs4(y, v));
     for (uint64_t i = nvec * 8 + tid; i < n; i += nthreads) {
         if (XOR) x0 ^= prod(x[i], y[i]);
         else s0 += prod(x[i], y[i]);
