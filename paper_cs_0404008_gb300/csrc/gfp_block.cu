@@ -589,10 +589,20 @@ __global__ void k_block_prep_b(const uint32_t *B, uint64_t ldb, uint64_t k, uint
     }
 }
 
+// x mod m for x < 2^40 and m < 2^17, minv = floor((2^64 - 1) / m): the
+// multiply-high quotient is floor(x / m) or one less
+__device__ __forceinline__ uint32_t mod_small64(uint64_t x, uint32_t m, uint64_t minv)
+{
+    const uint64_t r = x - __umul64hi(x, minv) * m;
+    return (uint32_t)(r >= m ? r - m : r);
+}
+
 // Garner recombination of L residue matrices R[l] (m x nb, dense) into
 // C = X mod p, where X is the unique integer in [0, prod m_l) with X = R[l]
 // mod m_l: mixed-radix digits v_l in [0, m_l), X = v_0 + m_0 (v_1 + m_1 (v_2
-// + ...)), evaluated modulo p from the innermost term out.
+// + ...)), evaluated modulo p from the innermost term out.  The moduli are
+// the largest primes <= 65791, all above 65000, so a digit v_j < m_j is below
+// 2 m_l and reduces modulo m_l by one conditional subtraction.
 __global__ void k_block_crt(const uint32_t *R, uint64_t m, uint64_t nb, uint32_t *C, uint64_t ldc, RnsConst rc)
 {
     const uint64_t count = m * nb;
@@ -603,12 +613,18 @@ __global__ void k_block_crt(const uint32_t *R, uint64_t m, uint64_t nb, uint32_t
         for (int l = 0; l < RNS_MAX; ++l) {
             if (l >= rc.L) break;
             const uint32_t ml = rc.mod[l];
-            uint64_t t = R[(uint64_t)l * count + e];
-            for (int j = 0; j < l; ++j) t = (t + ml - v[j] % ml) % ml * rc.inv[l][j] % ml;
-            v[l] = (uint32_t)t;
+            uint32_t t = R[(uint64_t)l * count + e];   // below ml
+#pragma unroll
+            for (int j = 0; j < RNS_MAX; ++j) {
+                if (j >= l) break;
+                const uint32_t vj = v[j] >= ml ? v[j] - ml : v[j];
+                t = t >= vj ? t - vj : t + ml - vj;     // (t - v_j) mod m_l
+                t = mod_small64((uint64_t)t * rc.inv[l][j], ml, rc.minv[l]);
+            }
+            v[l] = t;
         }
-        uint64_t acc = v[rc.L - 1] % rc.p;
-        for (int l = rc.L - 2; l >= 0; --l) acc = (acc * rc.mod[l] + v[l]) % rc.p;
+        uint64_t acc = reduce64(v[rc.L - 1], rc.modp);
+        for (int l = rc.L - 2; l >= 0; --l) acc = reduce64(acc * rc.mod[l] + v[l], rc.modp);
         C[(e / nb) * ldc + e % nb] = (uint32_t)acc;
     }
 }
@@ -736,7 +752,9 @@ bool block_rns_plan(uint32_t p, uint64_t k, RnsConst *rc)
         rc->mod[l] = l < L ? primes[l] : 1;
         for (int j = 0; j < RNS_MAX; ++j)
             rc->inv[l][j] = (l < L && j < l) ? pow_mod_small(primes[j], primes[l] - 2, primes[l]) : 0;
+        rc->minv[l] = UINT64_MAX / rc->mod[l];
     }
+    rc->modp = make_mod(p);
     return true;
 }
 

@@ -98,6 +98,8 @@ struct RnsConst {
     uint32_t p;
     uint32_t mod[RNS_MAX];
     uint32_t inv[RNS_MAX][RNS_MAX];
+    uint64_t minv[RNS_MAX];   // floor((2^64 - 1) / mod[l]), for remainders by multiply-high
+    Mod modp;                 // Barrett constants of p
 };
 // Chooses the moduli for k-term sums of products of residues below p; false
 // when RNS_MAX moduli do not cover k (p-1)^2.
