@@ -43,7 +43,7 @@ struct gfp_gfq {
     uint32_t *d_partials = nullptr;  // one per CTA of the dot kernel
     uint32_t *d_ticket = nullptr;    // finished CTAs (zero outside calls)
     uint32_t *d_err = nullptr;       // bit 0: a value >= q or a code > qbar was converted
-    uint16_t *d_exp16 = nullptr;     // 65536 entries: code -> element value (0 beyond qbar)
+    uint16_t *d_exp16 = nullptr;     // 65536 entries: code -> element value (entry 0: 1; 0 beyond qbar)
     unsigned long long *d_acc = nullptr;   // value-domain sum of the dot kernel (zero outside calls)
     int mode = 0;                    // 0: Zech additions; 1: integer sum (k = 1); 2: XOR (p = 2)
     int grid = 0;
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     // value of the product of codes a and b (0 if either is the zero element)
     auto prod = [&](uint32_t a, uint32_t b) -> uint32_t {
         uint32_t c = a + b;
-        c = c > qbar ? c - qbar : c;
+        c = min(c, c - qbar);   // a + b mod qbar, qbar itself becoming 0 (E[0] = E[qbar] = 1)
         const uint32_t v = E[c & 0xFFFFu];
         return (a == 0u || b == 0u) ? 0u : v;
     };
@@ -440,8 +440,11 @@ GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint
     }
     std::vector<uint32_t> expc(qbar + 1, 0);   // code -> value
     for (uint32_t c = 1; c <= qbar; ++c) expc[c] = expv[c % qbar];
-    std::vector<uint16_t> exp16(gfq::TABLE, 0);   // the same as uint16 (values < q <= 2^16)
+    // the same as uint16 (values < q <= 2^16); entry 0 holds x^0 = 1 like entry
+    // qbar, so that a product code reduced by min(c, c - qbar) may land on 0
+    std::vector<uint16_t> exp16(gfq::TABLE, 0);
     for (uint32_t c = 1; c <= qbar; ++c) exp16[c] = (uint16_t)expc[c];
+    exp16[0] = (uint16_t)expc[qbar];
 
     int sms = 0;
     GFQ_TRY(cudaSetDevice(device));
