@@ -95,8 +95,8 @@ __device__ __forceinline__ uint32_t zadd(uint32_t a, uint32_t c, const uint16_t 
 __device__ __forceinline__ uint32_t zstep(uint32_t acc, uint32_t a, uint32_t b, const uint16_t *Z,
                                           uint32_t qbar)
 {
-    uint32_t c = a + b;                         // code of the product (a, b >= 1)
-    c = c > qbar ? c - qbar : c;
+    uint32_t c = a + b;                         // code of the product (a, b >= 1), modulo qbar:
+    c = min(c, c - qbar);                       // qbar becomes 0, the same index below
     const uint32_t d = c - acc;                 // (c - acc) mod qbar by an unsigned min
     const uint32_t t = min(d, d + qbar);
     const uint32_t z = Z[t & 0xFFFFu];
