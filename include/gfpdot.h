@@ -265,8 +265,9 @@ GFP_API gfp_status gfp_matvec_sequence(gfp_ctx *ctx, uint32_t p, uint64_t n, con
  * primes <= 65791 whose product exceeds k (p-1)^2, each pass reducing the
  * inputs modulo its prime) and one launch recombining the residues with
  * Garner's method modulo p.  Otherwise the CUDA-core kernel with the
- * representation the context resolves for (p, k) (forcing F16TC where the
- * tensor cores are not eligible gives GFP_ERR_UNSUPPORTED).  The tensor-core path
+ * representation forced on the context, else the built-in rule for p (tuned
+ * plans time the dot-product kernels and do not apply here; forcing F16TC
+ * where the tensor cores are not eligible gives GFP_ERR_UNSUPPORTED).  The tensor-core path
  * uses the context's workspace (grown on demand, so call once outside stream
  * capture for the largest shape) and must not run concurrently with another
  * block product of the same context.  k == 0 writes zeros. */
@@ -280,7 +281,8 @@ GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64
  * row_ptr[i] <= q < row_ptr[i+1].  All arrays on the device; row_ptr must be
  * non-decreasing with row_ptr[0] = 0 (checked on the device only when
  * validation is enabled, together with col < k and the residues).  One launch;
- * k == 0 writes zeros. */
+ * k == 0 writes zeros.  Representation: the one forced on the context, else
+ * the built-in rule for p (tuned plans do not apply). */
 GFP_API gfp_status gfp_matmul_block_csr(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64_t k,
                                         uint64_t nb, const uint32_t *row_ptr, const uint32_t *col,
                                         const uint32_t *val, const uint32_t *B, uint64_t ldb,

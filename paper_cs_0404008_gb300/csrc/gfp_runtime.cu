@@ -160,6 +160,19 @@ static bool resolve_repr(const gfp_ctx *ctx, uint32_t requested, uint32_t p, uin
     return true;
 }
 
+// The same without the tuned plan: the plan times the dot-product kernels, so
+// products with other inner loops (sparse-row, CUDA-core block) take the
+// forced representation if one is set, else the built-in rule.
+static bool resolve_repr_untuned(const gfp_ctx *ctx, uint32_t p, Repr *out)
+{
+    uint32_t r = ctx ? ctx->forced : (uint32_t)GFP_REPR_AUTO;
+    if (r == GFP_REPR_AUTO) r = default_repr(p);
+    if (r < GFP_REPR_PERTERM || r >= GFP_REPR_COUNT_ || r == GFP_REPR_F16TC) return false;
+    if (!repr_eligible((Repr)r, p)) return false;
+    *out = (Repr)r;
+    return true;
+}
+
 static uint32_t chunk_for(const gfp_ctx *ctx, uint32_t p, uint64_t n)
 {
     const gfp_plan_entry *e = plan_lookup(ctx, p, n);
@@ -774,7 +787,7 @@ GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64
         use_tc = true;
     } else if (ctx->forced == GFP_REPR_AUTO && tc_ok) {
         use_tc = true;
-    } else if (!resolve_repr(ctx, GFP_REPR_AUTO, p, k, &r)) {
+    } else if (!resolve_repr_untuned(ctx, p, &r)) {
         return GFP_ERR_UNSUPPORTED;
     }
     if (ctx->validate) {
@@ -838,7 +851,7 @@ GFP_API gfp_status gfp_matmul_block_csr(gfp_ctx *ctx, uint32_t p, uint64_t m, ui
     if (m == 0 || nb == 0) return GFP_OK;
     cudaStream_t s = as_stream(stream);
     Repr r;
-    if (!resolve_repr(ctx, GFP_REPR_AUTO, p, k, &r)) return GFP_ERR_UNSUPPORTED;
+    if (!resolve_repr_untuned(ctx, p, &r)) return GFP_ERR_UNSUPPORTED;
     if (ctx->validate) {
         // structure: row_ptr read back on the host (validation mode synchronises anyway)
         std::vector<uint32_t> rp(m + 1);
