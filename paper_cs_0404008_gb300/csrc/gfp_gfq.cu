@@ -87,25 +87,48 @@ __device__ __forceinline__ uint32_t zadd(uint32_t a, uint32_t c, const uint16_t 
     return c == 0u ? a : r;
 }
 
-// acc + (code a) * (code b), for fields whose zero element is rare: the
-// common case (a, b, acc nonzero, no cancellation) without selects, and every
-// case involving the zero element (an input or the accumulator is zero, or
-// the sum cancels: Z[t] = 0) through the general code on one rarely taken
-// branch.  Codes are 1..qbar for nonzero elements, 0 for zero.
-__device__ __forceinline__ uint32_t zstep(uint32_t acc, uint32_t a, uint32_t b, const uint16_t *Z,
-                                          uint32_t qbar)
+// acc + (code a) * (code b) for fields whose zero element is rare, common
+// case only (a, b, acc nonzero, no cancellation), without selects: returns the
+// new code and sets m to a value that is 0 exactly when the case is not the
+// common one (a zero code, a zero accumulator, or Z[t] = 0 when the sum
+// cancels: a zero factor shows as a zero product, all four being below 2^16).
+// Codes are 1..qbar for nonzero elements, 0 for zero.
+__device__ __forceinline__ uint32_t zfast(uint32_t acc, uint32_t a, uint32_t b, const uint16_t *Z,
+                                          uint32_t qbar, uint32_t &m)
 {
-    uint32_t c = a + b;                         // code of the product (a, b >= 1), modulo qbar:
+    uint32_t c = a + b;                         // code of the product, modulo qbar:
     c = min(c, c - qbar);                       // qbar becomes 0, the same index below
     const uint32_t d = c - acc;                 // (c - acc) mod qbar by an unsigned min
     const uint32_t t = min(d, d + qbar);
     const uint32_t z = Z[t & 0xFFFFu];
     uint32_t r = acc + z;
     r = r > qbar ? r - qbar : r;
-    // a zero factor shows as a zero product (all four are below 2^16); the two
-    // multiplications run on the multiply-add pipe, off the busier integer ALU
-    if (min(a * b, acc * z) == 0u) r = zadd(acc, zmul(a, b, qbar), Z, qbar);
+    m = min(a * b, acc * z);
     return r;
+}
+
+// Four independent chains advanced by one term each, with one test for the
+// rare cases of all four (if any needs it, all four take the general code on
+// that rarely taken branch); the four common-case updates interleave.
+__device__ __forceinline__ void zstep4(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3,
+                                       uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1,
+                                       uint32_t a2, uint32_t b2, uint32_t a3, uint32_t b3,
+                                       const uint16_t *Z, uint32_t qbar)
+{
+    uint32_t m0, m1, m2, m3;
+    const uint32_t r0 = zfast(x0, a0, b0, Z, qbar, m0), r1 = zfast(x1, a1, b1, Z, qbar, m1);
+    const uint32_t r2 = zfast(x2, a2, b2, Z, qbar, m2), r3 = zfast(x3, a3, b3, Z, qbar, m3);
+    if (min(min(m0, m1), min(m2, m3)) == 0u) {
+        x0 = zadd(x0, zmul(a0, b0, qbar), Z, qbar);
+        x1 = zadd(x1, zmul(a1, b1, qbar), Z, qbar);
+        x2 = zadd(x2, zmul(a2, b2, qbar), Z, qbar);
+        x3 = zadd(x3, zmul(a3, b3, qbar), Z, qbar);
+    } else {
+        x0 = r0;
+        x1 = r1;
+        x2 = r2;
+        x3 = r3;
+    }
 }
 
 __device__ __forceinline__ uint32_t warp_zsum(uint32_t v, const uint16_t *Z, uint32_t qbar)
@@ -120,7 +143,7 @@ __device__ __forceinline__ uint4 ldcs4(const uint16_t *p, uint64_t v)
     return __ldcs(reinterpret_cast<const uint4 *>(p) + v);
 }
 
-// RARE: zstep (zero elements handled on a rare branch), for large fields;
+// RARE: zstep4 (zero elements handled on a rare branch), for large fields;
 // otherwise the select form of zadd(zmul), for small fields where zeros are
 // frequent enough to make the branch diverge.
 template <bool RARE>
@@ -144,14 +167,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint64_t nvec = vec ? n / 8 : 0;
     auto step = [&](const uint4 &u, const uint4 &w) {
         if constexpr (RARE) {
-            a0 = zstep(a0, u.x & 0xFFFFu, w.x & 0xFFFFu, Z, qbar);
-            a1 = zstep(a1, u.x >> 16, w.x >> 16, Z, qbar);
-            a2 = zstep(a2, u.y & 0xFFFFu, w.y & 0xFFFFu, Z, qbar);
-            a3 = zstep(a3, u.y >> 16, w.y >> 16, Z, qbar);
-            a0 = zstep(a0, u.z & 0xFFFFu, w.z & 0xFFFFu, Z, qbar);
-            a1 = zstep(a1, u.z >> 16, w.z >> 16, Z, qbar);
-            a2 = zstep(a2, u.w & 0xFFFFu, w.w & 0xFFFFu, Z, qbar);
-            a3 = zstep(a3, u.w >> 16, w.w >> 16, Z, qbar);
+            zstep4(a0, a1, a2, a3, u.x & 0xFFFFu, w.x & 0xFFFFu, u.x >> 16, w.x >> 16,
+                   u.y & 0xFFFFu, w.y & 0xFFFFu, u.y >> 16, w.y >> 16, Z, qbar);
+            zstep4(a0, a1, a2, a3, u.z & 0xFFFFu, w.z & 0xFFFFu, u.z >> 16, w.z >> 16,
+                   u.w & 0xFFFFu, w.w & 0xFFFFu, u.w >> 16, w.w >> 16, Z, qbar);
         } else {
             a0 = zadd(a0, zmul(u.x & 0xFFFFu, w.x & 0xFFFFu, qbar), Z, qbar);
             a1 = zadd(a1, zmul(u.x >> 16, w.x >> 16, qbar), Z, qbar);
