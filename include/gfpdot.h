@@ -441,7 +441,8 @@ GFP_API gfp_status gfp_gfq_find_primitive(uint32_t p, uint32_t k, uint32_t *f);
  * generate all q-1 non-zero elements modulo f (f reducible or not
  * primitive, or p not prime); GFP_ERR_NOMEM / GFP_ERR_CUDA on device
  * failures.  Device memory: two 128 KiB tables (Zech logarithms, code to
- * value) + 8 q bytes + scratch. */
+ * value) + 8 q bytes + scratch, plus 256 + q^2 bytes for odd p, k > 1 and
+ * q <= 256. */
 GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint32_t *f, gfp_gfq **out);
 GFP_API gfp_status gfp_gfq_destroy(gfp_gfq *fq);
 /* p, k and q = p^k of a field (any output pointer may be NULL). */
@@ -459,9 +460,10 @@ GFP_API gfp_status gfp_gfq_from_log(gfp_gfq *fq, uint64_t n, const uint16_t *cod
 /* *out (device) = code of sum_{i<n} x_i y_i in GF(q), x and y device arrays of
  * n codes in [0, q-1]; 16-byte aligned x and y take the vectorised path.
  * Each product is a code addition (Section 2.4); the sum is formed from
- * element values for prime fields (integers, reduced mod p once) and
- * characteristic 2 (XOR), and by Zech additions for odd characteristic with
- * k > 1.  n = 0 gives code 0.  Codes above q-1 are outside the contract: the
+ * element values for prime fields (integers, reduced mod p once),
+ * characteristic 2 (XOR) and odd characteristic with k > 1 and q <= 256 (a
+ * table of the field's value addition), and by Zech additions for larger odd
+ * characteristic extensions.  n = 0 gives code 0.  Codes above q-1 are outside the contract: the
  * result is then unspecified (no out-of-bounds access occurs). */
 GFP_API gfp_status gfp_gfq_dot(gfp_gfq *fq, uint64_t n, const uint16_t *x, const uint16_t *y, uint16_t *out,
                                void *stream);

@@ -45,7 +45,10 @@ struct gfp_gfq {
     uint32_t *d_err = nullptr;       // bit 0: a value >= q or a code > qbar was converted
     uint16_t *d_exp16 = nullptr;     // 65536 entries: code -> element value (entry 0: 1; 0 beyond qbar)
     unsigned long long *d_acc = nullptr;   // value-domain sum of the dot kernel (zero outside calls)
-    int mode = 0;                    // 0: Zech additions; 1: integer sum (k = 1); 2: XOR (p = 2)
+    uint8_t *d_tab8 = nullptr;       // q <= 256, k > 1: code -> value and value addition tables
+    uint32_t tab8_bytes = 0;
+    int mode = 0;                    // 0: Zech additions; 1: integer sum (k = 1); 2: XOR (p = 2);
+                                     // 3: value-addition table (odd p, k > 1, q <= 256)
     int grid = 0;
 };
 
@@ -318,6 +321,90 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
+// Value-domain dot product for small odd-characteristic extension fields
+// (k > 1, q <= 256): a product's code becomes its element value by one lookup
+// and values are added by one lookup in the q x q field-addition table, both
+// in shared memory: T[0, 256) code -> value (entry 0 holds x^0 = 1, entries
+// past q-1 hold 0), T[256 + s q + v] = value of s + v.  Four chains per
+// thread, then the warp, the CTA and the last CTA, all through the table.
+// Every table entry is below q, so indices stay inside it for any input.
+__global__ void __launch_bounds__(THREADS, 1)
+    k_gfq_dot_add(const uint16_t *__restrict__ x, const uint16_t *__restrict__ y, uint64_t n, int vec,
+                  const uint8_t *__restrict__ Tg, uint32_t tbytes, uint32_t q, uint32_t qbar,
+                  const uint32_t *__restrict__ logt, uint32_t *partials, uint32_t *ticket, uint16_t *out)
+{
+    extern __shared__ uint8_t T[];
+    __shared__ uint32_t wpart[THREADS / 32];
+    __shared__ uint32_t last;
+    for (uint32_t i = threadIdx.x; i < tbytes / 16u; i += blockDim.x)
+        reinterpret_cast<uint4 *>(T)[i] = reinterpret_cast<const uint4 *>(Tg)[i];
+    __syncthreads();
+    const uint8_t *E = T, *ADD = T + 256;
+
+    auto prod = [&](uint32_t a, uint32_t b) -> uint32_t {
+        uint32_t c = a + b;
+        c = min(c, c - qbar);   // a + b mod qbar, qbar itself becoming 0 (E[0] = 1)
+        const uint32_t v = E[c & 0xFFu];
+        return (a == 0u || b == 0u) ? 0u : v;
+    };
+    auto add = [&](uint32_t s, uint32_t v) -> uint32_t { return ADD[s * q + v]; };
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    auto step = [&](const uint4 &u, const uint4 &w) {
+        s0 = add(s0, prod(u.x & 0xFFFFu, w.x & 0xFFFFu));
+        s1 = add(s1, prod(u.x >> 16, w.x >> 16));
+        s2 = add(s2, prod(u.y & 0xFFFFu, w.y & 0xFFFFu));
+        s3 = add(s3, prod(u.y >> 16, w.y >> 16));
+        s0 = add(s0, prod(u.z & 0xFFFFu, w.z & 0xFFFFu));
+        s1 = add(s1, prod(u.z >> 16, w.z >> 16));
+        s2 = add(s2, prod(u.w & 0xFFFFu, w.w & 0xFFFFu));
+        s3 = add(s3, prod(u.w >> 16, w.w >> 16));
+    };
+    const uint64_t nvec = vec ? n / 8 : 0;
+    uint64_t v = tid;
+    for (; v + (GFQ_NS - 1) * nthreads < nvec; v += GFQ_NS * nthreads) {
+        uint4 u[GFQ_NS], w[GFQ_NS];
+#pragma unroll
+        for (int j = 0; j < GFQ_NS; ++j) {
+            u[j] = ldcs4(x, v + j * nthreads);
+            w[j] = ldcs4(y, v + j * nthreads);
+        }
+#pragma unroll
+        for (int j = 0; j < GFQ_NS; ++j) step(u[j], w[j]);
+    }
+    for (; v < nvec; v += nthreads) step(ldcs4(x, v), ldcs4(y, v));
+    for (uint64_t i = nvec * 8 + tid; i < n; i += nthreads) s0 = add(s0, prod(x[i], y[i]));
+    uint32_t acc = add(add(s0, s1), add(s2, s3));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc = add(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    if (lane == 0) wpart[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        acc = lane < (int)(blockDim.x >> 5) ? wpart[lane] : 0u;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc = add(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+        if (lane == 0) {
+            partials[blockIdx.x] = acc;
+            __threadfence();
+            last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    if (last && warp == 0) {
+        __threadfence();
+        acc = 0;
+        for (uint32_t b = lane; b < gridDim.x; b += 32) acc = add(acc, __ldcg(partials + b));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc = add(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+        if (lane == 0) {
+            *out = (uint16_t)logt[acc];
+            *ticket = 0u;   // ready for the next call
+        }
+    }
+}
+
 __global__ void k_gfq_to_log(const uint32_t *__restrict__ v, uint64_t n, const uint32_t *__restrict__ logt,
                              uint32_t q, uint16_t *__restrict__ codes, uint32_t *err)
 {
@@ -465,6 +552,21 @@ GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint
     std::vector<uint16_t> exp16(gfq::TABLE, 0);
     for (uint32_t c = 1; c <= qbar; ++c) exp16[c] = (uint16_t)expc[c];
     exp16[0] = (uint16_t)expc[qbar];
+    // small odd-characteristic extensions: code -> value (uint8) and the value
+    // addition table (digit-wise sums mod p of the base-p values)
+    const bool small_ext = p != 2 && k > 1 && q <= 256;
+    std::vector<uint8_t> tab8;
+    if (small_ext) {
+        tab8.assign(((size_t)256 + (size_t)q * q + 15) & ~(size_t)15, 0);
+        for (uint32_t c = 1; c <= qbar; ++c) tab8[c] = (uint8_t)expc[c];
+        tab8[0] = (uint8_t)expc[qbar];
+        for (uint32_t a = 0; a < q; ++a)
+            for (uint32_t b = 0; b < q; ++b) {
+                uint32_t r = 0, pw = 1, u = a, w = b;
+                for (uint32_t j = 0; j < k; ++j, pw *= p, u /= p, w /= p) r += ((u % p + w % p) % p) * pw;
+                tab8[256 + (size_t)a * q + b] = (uint8_t)r;
+            }
+    }
 
     int sms = 0;
     GFQ_TRY(cudaSetDevice(device));
@@ -477,6 +579,8 @@ GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint
                                  (int)gfq::SMEM));
     GFQ_TRY(cudaFuncSetAttribute(gfq::k_gfq_dot_exp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)gfq::SMEM));
+    GFQ_TRY(cudaFuncSetAttribute(gfq::k_gfq_dot_add, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 256 + 256 * 256));
     gfp_gfq *fq = new gfp_gfq;
     fq->device = device;
     fq->p = p;
@@ -485,7 +589,7 @@ GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint
     fq->qbar = qbar;
     for (uint32_t j = 0; j < k; ++j) fq->f[j] = f[j];
     fq->grid = std::max(1, sms);
-    fq->mode = p == 2 ? 2 : (k == 1 ? 1 : 0);
+    fq->mode = p == 2 ? 2 : (k == 1 ? 1 : (small_ext ? 3 : 0));
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void **ptr, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
@@ -498,6 +602,10 @@ GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint
     alloc((void **)&fq->d_err, 4);
     alloc((void **)&fq->d_exp16, gfq::SMEM);
     alloc((void **)&fq->d_acc, 8);
+    if (small_ext) {
+        fq->tab8_bytes = (uint32_t)tab8.size();
+        alloc((void **)&fq->d_tab8, tab8.size());
+    }
     if (e == cudaSuccess) e = cudaMemcpy(fq->d_zech, zech.data(), gfq::SMEM, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(fq->d_log, logv.data(), (size_t)q * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(fq->d_exp, expc.data(), (size_t)(qbar + 1) * 4, cudaMemcpyHostToDevice);
@@ -505,6 +613,8 @@ GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint
     if (e == cudaSuccess) e = cudaMemset(fq->d_err, 0, 4);
     if (e == cudaSuccess) e = cudaMemcpy(fq->d_exp16, exp16.data(), gfq::SMEM, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(fq->d_acc, 0, 8);
+    if (e == cudaSuccess && small_ext)
+        e = cudaMemcpy(fq->d_tab8, tab8.data(), tab8.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         note_cuda_error(e);
         gfp_gfq_destroy(fq);
@@ -525,6 +635,7 @@ GFP_API gfp_status gfp_gfq_destroy(gfp_gfq *fq)
     cudaFree(fq->d_ticket);
     cudaFree(fq->d_err);
     cudaFree(fq->d_exp16);
+    cudaFree(fq->d_tab8);
     cudaFree(fq->d_acc);
     delete fq;
     return GFP_OK;
@@ -589,6 +700,10 @@ GFP_API gfp_status gfp_gfq_dot(gfp_gfq *fq, uint64_t n, const uint16_t *x, const
     else if (fq->mode == 2)
         gfq::k_gfq_dot_exp<true><<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_exp16, fq->qbar, fq->p,
                                                                         fq->d_log, fq->d_acc, fq->d_ticket, out);
+    else if (fq->mode == 3)
+        gfq::k_gfq_dot_add<<<grid, gfq::THREADS, fq->tab8_bytes, s>>>(x, y, n, vec, fq->d_tab8, fq->tab8_bytes,
+                                                                       fq->q, fq->qbar, fq->d_log, fq->d_partials,
+                                                                       fq->d_ticket, out);
     else if (fq->q >= gfq::RARE_Q)
         gfq::k_gfq_dot<true><<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_zech, fq->qbar,
                                                                     fq->d_partials, fq->d_ticket, out);

@@ -13,7 +13,7 @@ from paper_cs_0404008_gb300 import gfpdot as g
 pytestmark = pytest.mark.gpu
 
 FIELDS = [(2, 1), (3, 1), (2, 8), (3, 2), (5, 3), (17, 3), (13, 4), (251, 1), (65521, 1),
-          (3, 10), (2, 16), (5, 6), (7, 5), (3, 7), (13, 3)]
+          (3, 10), (2, 16), (5, 6), (7, 5), (3, 7), (13, 3), (7, 2), (11, 2), (3, 5)]
 _F = {}
 
 
@@ -116,7 +116,7 @@ def test_products_and_cancellation():
             fq.close()
 
 
-@pytest.mark.parametrize("p,k", [(3, 2), (5, 3), (3, 7), (17, 3), (13, 4), (3, 10), (5, 6), (7, 5)])
+@pytest.mark.parametrize("p,k", [(3, 2), (5, 3), (3, 5), (3, 7), (17, 3), (13, 4), (3, 10), (5, 6), (7, 5)])
 def test_accumulator_chains_cancel_and_restart(p, k):
     """Codes 8j+i and 8j+i+4 carry v*1 and v*(-1), so each of a thread's four
     accumulator chains returns to the zero element after every 8-code step
