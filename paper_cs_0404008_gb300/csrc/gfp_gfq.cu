@@ -59,9 +59,9 @@ constexpr int THREADS = 1024;
 constexpr uint32_t TABLE = 65536;
 constexpr size_t SMEM = TABLE * sizeof(uint16_t);   // 128 KiB
 // fields from this size on take the Zech kernel with the rare zero branch
-// (measured: faster from q = 2187 on, slower at q = 729, where a warp's four
-// updates of 32 lanes meet a zero element too often)
-constexpr uint32_t RARE_Q = 2048;
+// (measured at 2^27 codes: faster from q = 1331 on, slower up to q = 729,
+// where a warp's four updates of 32 lanes meet a zero element too often)
+constexpr uint32_t RARE_Q = 1024;
 // grid strides per loop iteration: with one 1024-thread CTA per SM (the table
 // takes 128 KiB of shared memory) and 64 registers per thread, eight 16-byte
 // loads in flight per thread are what keeps HBM busy (one stride: 0.75-0.77 of

@@ -13,7 +13,7 @@ from paper_cs_0404008_gb300 import gfpdot as g
 pytestmark = pytest.mark.gpu
 
 FIELDS = [(2, 1), (3, 1), (2, 8), (3, 2), (5, 3), (17, 3), (13, 4), (251, 1), (65521, 1),
-          (3, 10), (2, 16), (5, 6), (7, 5), (3, 7), (13, 3), (7, 2), (11, 2), (3, 5)]
+          (3, 10), (2, 16), (5, 6), (7, 5), (3, 7), (13, 3), (7, 2), (11, 2), (3, 5), (11, 3)]
 _F = {}
 
 
