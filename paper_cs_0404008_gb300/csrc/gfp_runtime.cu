@@ -165,7 +165,7 @@ static bool resolve_repr(const gfp_ctx *ctx, uint32_t requested, uint32_t p, uin
 // forced representation if one is set, else the built-in rule.
 static bool resolve_repr_untuned(const gfp_ctx *ctx, uint32_t p, Repr *out)
 {
-    uint32_t r = ctx ? ctx->forced : (uint32_t)GFP_REPR_AUTO;
+    uint32_t r = ctx ? (uint32_t)ctx->forced : (uint32_t)GFP_REPR_AUTO;
     if (r == GFP_REPR_AUTO) r = default_repr(p);
     if (r < GFP_REPR_PERTERM || r >= GFP_REPR_COUNT_ || r == GFP_REPR_F16TC) return false;
     if (!repr_eligible((Repr)r, p)) return false;
