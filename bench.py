@@ -520,6 +520,14 @@ def run_secondary(args):
 
 
 GFQ_FIELDS = [(2, 8), (3, 10), (65521, 1)]
+
+
+def gfq_kernel(p: int, k: int) -> str:
+    """The kernel the library runs for GF(p^k) (values summed for prime fields,
+    characteristic 2 and small odd extensions, Zech additions otherwise)."""
+    if p == 2 or k == 1:
+        return "k_gfq_dot_exp"
+    return "k_gfq_dot_add" if p ** k <= 256 else "k_gfq_dot"
 GFQ_N = 1 << 27
 
 
@@ -529,7 +537,10 @@ def measure_gfq(args, g, torch, stream, line, peak, peak_kind):
     dot product; 4 bytes read per multiply-add."""
     res = {}
     n = GFQ_N
-    for p, k in GFQ_FIELDS:
+    fields = GFQ_FIELDS
+    if args.gfq_fields:
+        fields = [tuple(int(t) for t in f.split("^")) for f in args.gfq_fields.split(",")]
+    for p, k in fields:
         q = p ** k
         f = g.gfp_gfq_find_primitive(p, k)
         fq = g.Field(p, k, f)
@@ -558,7 +569,7 @@ def measure_gfq(args, g, torch, stream, line, peak, peak_kind):
         t = e0.elapsed_time(e1) / reps
         gbs = 4.0 * n / (t / 1e3) / 1e9
         res[f"GF({p}^{k})"] = {"q": q, "ms": t, "gmacs": n / (t / 1e3) / 1e9, "gbs": gbs,
-                               "frac": gbs / peak}
+                               "frac": gbs / peak, "kernel": gfq_kernel(p, k)}
         fq.close()
         del X, Y
         torch.cuda.empty_cache()
@@ -568,11 +579,11 @@ def measure_gfq(args, g, torch, stream, line, peak, peak_kind):
         "value": worst["gmacs"], "ms_per_step": worst["ms"],
         "config": {"workload": "dot products over GF(q) in the discrete-logarithm (Zech) "
                                "representation, 2^27 uint16 codes per vector, uniform elements, "
-                               "fields GF(2^8), GF(3^10), GF(65521)",
+                               "fields " + ", ".join(res),
                    "value_is": "the slowest field"},
         "roofline": {"bound": "hbm", "achieved": worst["gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": worst["frac"], "kernel": "k_gfq_dot",
-                     "traffic": traffic_for("k_gfq_dot", 4.0 * n),
+                     "frac": worst["frac"], "kernel": worst["kernel"],
+                     "traffic": traffic_for(worst["kernel"], 4.0 * n),
                      "peak_kind": f"{peak_kind} hbm_gbs", "best_field_frac": best["frac"]},
         "fields": res,
         "gpu_launches": 1,
@@ -1174,6 +1185,8 @@ def main():
     ap.add_argument("--requests", type=int, default=20000, help="serve: Poisson requests")
     ap.add_argument("--load", type=float, default=0.7, help="serve: arrival rate / capacity")
     ap.add_argument("--block-m", type=int, default=16384, help="block workload rows (profiling)")
+    ap.add_argument("--gfq-fields", default=None,
+                    help="gfq workload: comma-separated fields p^k (default 2^8,3^10,65521^1)")
     ap.add_argument("--block-p", type=int, default=65521,
                     help="block workload prime; above 65791 the product runs through residue passes")
     ap.add_argument("--mv-n", type=int, default=32768, help="matvec side (profiling)")
