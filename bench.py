@@ -54,6 +54,31 @@ def hbm_peak():
     return 6800.0, "fallback"
 
 
+_OWN_PEAKS = {}
+
+
+def own_peaks() -> dict:
+    """Ceilings measured in this run by the project's own probe kernels
+    (libgfppeaks): a read-only HBM stream (the ceiling of kernels that only
+    read, as the dot products do), L2-to-SM reads and the DFMA rate.  Measured
+    once per process, after the clock-sampled load phase."""
+    if not _OWN_PEAKS:
+        from paper_cs_0404008_gb300 import peaks as pk
+        for kind, nb, reps in (("read_hbm", 4 << 30, 12), ("read_l2", 64 << 20, 8), ("dfma", 0, 4)):
+            r = pk.measure(kind, nb, reps)
+            _OWN_PEAKS[kind] = {"peak": r["rate"], "unit": r["unit"],
+                                "source": f"libgfppeaks {kind} (best of {reps}), this run"}
+    return _OWN_PEAKS
+
+
+def with_read_peak(roof: dict) -> dict:
+    """Adds the fraction of the measured read-only stream ceiling to an HBM roofline."""
+    rp = own_peaks()["read_hbm"]
+    roof["read_stream"] = {"peak": rp["peak"], "frac": roof["achieved"] / rp["peak"],
+                           "unit": "GB/s", "source": rp["source"]}
+    return roof
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -327,6 +352,13 @@ def run_gpu(args):
             macs = float(sel.sum())
             extra[name] = {"gmacs": macs * 10 / (ms / 1e3) / 1e9, "ms_per_launch": ms / 10,
                            "gbs": (8 * macs) * 10 / (ms / 1e3) / 1e9}
+            if rp == g.GFP_REPR_FP64:
+                # one fma (2 flops) per multiply-add: the FP64 loop's own roofline
+                dp = own_peaks()["dfma"]
+                tf = 2 * macs * 10 / (ms / 1e3) / 1e12
+                extra[name]["dfma"] = {"bound": "alu", "achieved": tf, "peak": dp["peak"],
+                                       "unit": "TFLOP/s", "frac": tf / dp["peak"],
+                                       "source": dp["source"]}
             pl.close()
         # tuned vs per-term speed-up on identical exact results
         extra["tuned_over_perterm"] = value / world / extra["perterm"]["gmacs"]
@@ -397,11 +429,11 @@ def run_gpu(args):
         sv = measure_serve(args, g)
         also["serve"] = {"value": sv["value"], "unit": sv["unit"], "config": sv["config"],
                          **sv["serve"]}
-        # the same service at 50 % and 90 % of its measured capacity (shorter streams)
+        # the same service at 50 % and 90 % of its measured capacity, same stream length
         sweep = {}
         for ld in (0.5, 0.9):
             a2 = argparse.Namespace(**vars(args))
-            a2.load, a2.requests = ld, min(args.requests, 10000)
+            a2.load = ld
             s2 = measure_serve(a2, g)["serve"]
             sweep[f"{int(ld * 100)}%"] = {k: s2[k] for k in ("p50_ms", "p99_ms", "achieved_jobs_per_s",
                                                              "all_ok", "verify_mismatches")}
@@ -421,13 +453,14 @@ def run_gpu(args):
                        "tune_seconds": round(t_tune, 2),
                        "plan": "built-in rules" if args.no_tune else "tuned at setup"},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy test)",
-                         "kernel": "k_dot_batched",
-                         "traffic": (trec["dram_bytes_per_algorithmic_byte"] * batch.bytes
-                                     if trec else None),
-                         "traffic_source": ("ncu dram bytes of a 512-pair capture, scaled by "
-                                            "algorithmic bytes" if trec else None)},
+            "roofline": with_read_peak(
+                {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                 "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy test)",
+                 "kernel": "k_dot_batched",
+                 "traffic": (trec["dram_bytes_per_algorithmic_byte"] * batch.bytes
+                             if trec else None),
+                 "traffic_source": ("ncu dram bytes of a 512-pair capture, scaled by "
+                                    "algorithmic bytes" if trec else None)}),
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -581,10 +614,11 @@ def measure_gfq(args, g, torch, stream, line, peak, peak_kind):
                                "representation, 2^27 uint16 codes per vector, uniform elements, "
                                "fields " + ", ".join(res),
                    "value_is": "the slowest field"},
-        "roofline": {"bound": "hbm", "achieved": worst["gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": worst["frac"], "kernel": worst["kernel"],
-                     "traffic": traffic_for(worst["kernel"], 4.0 * n),
-                     "peak_kind": f"{peak_kind} hbm_gbs", "best_field_frac": best["frac"]},
+        "roofline": with_read_peak(
+            {"bound": "hbm", "achieved": worst["gbs"], "peak": peak, "unit": "GB/s",
+             "frac": worst["frac"], "kernel": worst["kernel"],
+             "traffic": traffic_for(worst["kernel"], 4.0 * n),
+             "peak_kind": f"{peak_kind} hbm_gbs", "best_field_frac": best["frac"]}),
         "fields": res,
         "gpu_launches": 1,
     })
@@ -668,11 +702,12 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                          "speedup_over_perterm": t_pt / t_batch},
             "graph_of_256_single_dots": {"ms": t_graph, "gmacs": gm(t_graph),
                                           "gbs": 8 * macs / (t_graph / 1e3) / 1e9},
-            "roofline": {"bound": "hbm", "achieved": 8 * macs / (t_batch / 1e3) / 1e9, "peak": peak,
-                         "unit": "GB/s", "frac": 8 * macs / (t_batch / 1e3) / 1e9 / peak,
-                         "kernel": "k_dot_batched",
-                         "traffic": traffic_for("k_dot_batched", 8 * macs + 4.0 * nvec),
-                         "peak_kind": f"{peak_kind} hbm_gbs"},
+            "roofline": with_read_peak(
+                {"bound": "hbm", "achieved": 8 * macs / (t_batch / 1e3) / 1e9, "peak": peak,
+                 "unit": "GB/s", "frac": 8 * macs / (t_batch / 1e3) / 1e9 / peak,
+                 "kernel": "k_dot_batched",
+                 "traffic": traffic_for("k_dot_batched", 8 * macs + 4.0 * nvec),
+                 "peak_kind": f"{peak_kind} hbm_gbs"}),
             "gpu_launches": len(per),
         })
         plan.close()
@@ -707,10 +742,11 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
             "config": {"workload": f"Wiedemann iteration over GF(2147483647): A {n}x{n} uint32 "
                                    f"uniform, x_(t+1) = A x_t for {iters} iterations in one CUDA graph",
                        "l2": "A is 4 GiB, larger than L2"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "kernel": "k_matvec",
-                         "traffic": traffic_for("k_matvec", 4.0 * n * n + 8.0 * n),
-                         "peak_kind": f"{peak_kind} hbm_gbs"},
+            "roofline": with_read_peak(
+                {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                 "frac": achieved / peak, "kernel": "k_matvec",
+                 "traffic": traffic_for("k_matvec", 4.0 * n * n + 8.0 * n),
+                 "peak_kind": f"{peak_kind} hbm_gbs"}),
             "same_gpu": {"perterm_ms": res["perterm"],
                          "perterm_gmacs": macs / (res["perterm"] / 1e3) / 1e9,
                          "speedup_over_perterm": res["perterm"] / t},
@@ -814,6 +850,10 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
             del flush
             cmacs = float(nnz) * nb
             abytes = 8.0 * nnz + 4.0 * (m + 1) + 4.0 * k * nb + 4.0 * m * nb
+            # gathers from L2: one B row (nb stored elements) per nonzero
+            csr_kernel, bpe = ("k_block_csr_h16", 2) if p <= 65536 else ("k_block_csr_wide", 4)
+            gbytes = float(nnz) * nb * bpe
+            l2p = own_peaks()["read_l2"]
             line.update({
                 "value": cmacs / (t / 1e3) / 1e9, "ms_per_step": t,
                 "config": {"workload": f"sparse-row block product over GF(65521): CSR A {m}x{k} with "
@@ -822,10 +862,17 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                            "l2": "flushed before each timed product (inputs 26 MB fit L2)"},
                 "roofline": {"bound": "hbm", "achieved": abytes / (t / 1e3) / 1e9, "peak": peak,
                              "unit": "GB/s", "frac": abytes / (t / 1e3) / 1e9 / peak,
-                             "kernel": "k_block_csr_wide",
-                             "traffic": traffic_for("k_block_csr_wide", abytes),
+                             "kernel": csr_kernel,
+                             "traffic": traffic_for(csr_kernel, abytes),
                              "peak_kind": f"{peak_kind} hbm_gbs",
-                             "note": "B (4 MiB) is re-read from L2 per nonzero; HBM bytes count it once"},
+                             "note": "B is re-read from L2 per nonzero; HBM bytes count it once",
+                             "l2": {"bound": "l2", "achieved": gbytes / (t / 1e3) / 1e9,
+                                    "peak": l2p["peak"], "unit": "GB/s",
+                                    "frac": gbytes / (t / 1e3) / 1e9 / l2p["peak"],
+                                    "bytes_per_launch": gbytes,
+                                    "what": f"B-row gathers: {bpe} bytes per stored B element, "
+                                            "nb elements per nonzero",
+                                    "source": l2p["source"]}},
                 "gpu_launches": 1,
             })
     torch.cuda.synchronize()
@@ -835,25 +882,6 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
 # ---------------------------------------------------------------------------
 # serving: Poisson stream of mixed jobs through the continuous-batching server
 # ---------------------------------------------------------------------------
-
-def serve_requests(count: int, seed: int):
-    """Seeded request mix: 70% dot (n log-uniform [2^10, 2^22]), 25% matvec,
-    5% block over pools of 16 registered matrices per kind; primes uniform over
-    {65521, 67108859, 4294967291}."""
-    u = gi.unit_doubles(seed, 10, count)
-    v = gi.unit_doubles(seed, 11, count)
-    w = gi.words(seed, 12, count)
-    kinds = np.where(u < 0.70, 0, np.where(u < 0.95, 1, 2))
-    reqs = []
-    for i in range(count):
-        k = int(kinds[i])
-        if k == 0:
-            n = int(np.floor(2.0 ** (10 + 12 * v[i])))
-            reqs.append((0, gi.PRIMES_SERVE[int(w[i] % np.uint64(3))], n, 0, seed * 1000003 + i))
-        else:
-            reqs.append((k, None, 0, int(w[i] % np.uint64(16)), seed * 1000003 + i))
-    return reqs
-
 
 def run_serve(args):
     import torch
@@ -870,17 +898,10 @@ def measure_serve(args, g):
     srv = g.Server(device=0, mem_budget=16 << 30, n_streams=8, batch_window_us=50,
                    max_inflight=256)
     # resident matrix pools (registered once): sides log-uniform
-    pools = {1: [], 2: []}
-    for kind, lo, hi in ((1, 10, 14), (2, 10, 13)):
-        du = gi.unit_doubles(seed, 20 + kind, 16)
-        dw = gi.words(seed, 22 + kind, 16)
-        for i in range(16):
-            side = int(np.floor(2.0 ** (lo + (hi - lo) * du[i])))
-            p = gi.PRIMES_SERVE[int(dw[i] % np.uint64(3))]
-            mseed = seed * 7919 + kind * 100 + i
-            h = srv.register_matrix(p, side, side, seed=mseed)
-            pools[kind].append((h, p, side, mseed))
-    reqs = serve_requests(args.requests, seed)
+    pools = {kind: [(srv.register_matrix(p, side, side, seed=mseed), p, side, mseed)
+                    for p, side, mseed in specs]
+             for kind, specs in gi.serve_pool_specs(seed).items()}
+    reqs = gi.serve_requests(args.requests, seed)
 
     def submit(r):
         k, p, n, mi, sd = r
@@ -922,7 +943,8 @@ def measure_serve(args, g):
         for i in range(len(reqs)):
             ready.acquire()
             st, res = srv.wait(tickets[i], 600_000_000)
-            results[i] = (st, res.status, res.value, res.t_submit_ns, res.t_done_ns, res.batch)
+            results[i] = (st, res.status, res.value, res.t_submit_ns, res.t_done_ns, res.batch,
+                          res.t_admit_ns, res.t_start_ns)
             if i in sample and res.status == g.GFP_OK and reqs[i][0] != 0:
                 outs[i] = srv.result_copy(tickets[i], res.out_elems)
             srv.release(tickets[i])
@@ -949,12 +971,23 @@ def measure_serve(args, g):
     # latency by job kind (and, for block jobs, by whether the tensor-core path applies)
     by_kind = {}
     kinds = np.array([r[0] for r in reqs])
+    # where the time goes: queued (submit -> admit), launching (admit -> launch
+    # calls returned), on the device until the dispatcher saw it done
+    queued = np.array([(x[6] - x[3]) / 1e6 for x in results])
+    launching = np.array([(x[7] - x[6]) / 1e6 for x in results])
+    running = np.array([(x[4] - x[7]) / 1e6 for x in results])
     for kname, kid in (("dot", 0), ("matvec", 1), ("block", 2)):
         sel = kinds == kid
         if sel.any():
             by_kind[kname] = {"count": int(sel.sum()), "p50_ms": float(np.percentile(lat[sel], 50)),
                               "p99_ms": float(np.percentile(lat[sel], 99)),
-                              "max_ms": float(lat[sel].max())}
+                              "max_ms": float(lat[sel].max()),
+                              "stages_p50_ms": {"queued": float(np.percentile(queued[sel], 50)),
+                                                "launching": float(np.percentile(launching[sel], 50)),
+                                                "running": float(np.percentile(running[sel], 50))},
+                              "stages_p99_ms": {"queued": float(np.percentile(queued[sel], 99)),
+                                                "launching": float(np.percentile(launching[sel], 99)),
+                                                "running": float(np.percentile(running[sel], 99))}}
     top = np.argsort(lat)[-max(1, len(lat) // 100):]
     by_kind["slowest_1pct_kinds"] = {kname: int((kinds[top] == kid).sum())
                                      for kname, kid in (("dot", 0), ("matvec", 1), ("block", 2))}
@@ -1182,7 +1215,7 @@ def main():
     ap.add_argument("--sweep-points", type=int, default=24,
                     help="cpu_sweep: log-spaced primes per word size")
     ap.add_argument("--sweep-table", default=None, help="cpu_sweep: also write a markdown table")
-    ap.add_argument("--requests", type=int, default=20000, help="serve: Poisson requests")
+    ap.add_argument("--requests", type=int, default=100000, help="serve: Poisson requests")
     ap.add_argument("--load", type=float, default=0.7, help="serve: arrival rate / capacity")
     ap.add_argument("--block-m", type=int, default=16384, help="block workload rows (profiling)")
     ap.add_argument("--gfq-fields", default=None,

@@ -176,3 +176,42 @@ def csr_pattern(m: int, k: int, density: float, p: int, seed: int):
     col = np.concatenate(rows_col) if rows_col else np.zeros(0, np.uint32)
     val = np.concatenate(rows_val) if rows_val else np.zeros(0, np.uint32)
     return row_ptr, col.astype(np.uint32), val.astype(np.uint32)
+
+
+def serve_requests(count: int, seed: int):
+    """Seeded request mix of the serving workload: 70% dot (n log-uniform
+    [2^10, 2^22], p uniform over PRIMES_SERVE), 25% matrix-vector and 5% block
+    jobs over pools of 16 registered matrices per kind (see serve_pool_specs).
+    Request i is (kind, p or None, n, pool index, job seed); kind 0 dot,
+    1 matrix-vector, 2 block.  The first c requests of a longer stream are the
+    requests of serve_requests(c, seed)."""
+    u = unit_doubles(seed, 10, count)
+    v = unit_doubles(seed, 11, count)
+    w = words(seed, 12, count)
+    kinds = np.where(u < 0.70, 0, np.where(u < 0.95, 1, 2))
+    reqs = []
+    for i in range(count):
+        k = int(kinds[i])
+        if k == 0:
+            n = int(np.floor(2.0 ** (10 + 12 * v[i])))
+            reqs.append((0, PRIMES_SERVE[int(w[i] % np.uint64(3))], n, 0, seed * 1000003 + i))
+        else:
+            reqs.append((k, None, 0, int(w[i] % np.uint64(16)), seed * 1000003 + i))
+    return reqs
+
+
+def serve_pool_specs(seed: int):
+    """The registered matrices of the serving workload: for kind 1
+    (matrix-vector) 16 square matrices with side log-uniform [2^10, 2^14], for
+    kind 2 (block, nb = 64) 16 with side log-uniform [2^10, 2^13]; p uniform
+    over PRIMES_SERVE.  Returns {kind: [(p, side, matrix seed)] * 16}; matrix
+    entries are uniform(p, side*side, matrix seed, 0) in row-major order."""
+    pools = {1: [], 2: []}
+    for kind, lo, hi in ((1, 10, 14), (2, 10, 13)):
+        du = unit_doubles(seed, 20 + kind, 16)
+        dw = words(seed, 22 + kind, 16)
+        for i in range(16):
+            side = int(np.floor(2.0 ** (lo + (hi - lo) * du[i])))
+            p = PRIMES_SERVE[int(dw[i] % np.uint64(3))]
+            pools[kind].append((p, side, seed * 7919 + kind * 100 + i))
+    return pools

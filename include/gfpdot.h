@@ -280,9 +280,14 @@ GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64
  * k x nb dense.  C[i*ldc + j] = (sum_q val[q] * B[col[q]*ldb + j]) mod p for
  * row_ptr[i] <= q < row_ptr[i+1].  All arrays on the device; row_ptr must be
  * non-decreasing with row_ptr[0] = 0 (checked on the device only when
- * validation is enabled, together with col < k and the residues).  One launch;
- * k == 0 writes zeros.  Representation: the one forced on the context, else
- * the built-in rule for p (tuned plans do not apply). */
+ * validation is enabled, together with col < k and the residues).  One launch,
+ * or two when p <= 65536, nb is a multiple of 8 and the blocked representation
+ * applies: B is then first packed to 16 bits per residue in a context
+ * workspace (k * nb * 2 bytes, grown by the first call that needs more, so
+ * make that call outside stream capture), which halves the bytes of the B-row
+ * gathers.  k == 0 writes zeros.  Representation: the one forced on the
+ * context, else the built-in rule for p (tuned plans do not apply).  Calls
+ * sharing one context must not run concurrently on different streams. */
 GFP_API gfp_status gfp_matmul_block_csr(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64_t k,
                                         uint64_t nb, const uint32_t *row_ptr, const uint32_t *col,
                                         const uint32_t *val, const uint32_t *B, uint64_t ldb,
@@ -371,7 +376,9 @@ typedef struct gfp_result {
     uint32_t value;             /* DOT: the residue */
     uint32_t batch;             /* DOT: number of dot jobs that shared its launch */
     uint64_t out_elems;         /* MATVEC / BLOCK: output residues held for gfp_result_copy */
-    uint64_t t_submit_ns, t_admit_ns, t_start_ns, t_done_ns;   /* CLOCK_MONOTONIC */
+    uint64_t t_submit_ns, t_admit_ns, t_start_ns, t_done_ns;   /* steady clock: submitted,
+                                   admitted, its launches enqueued on the GPU (simulation: launch
+                                   decided), completion seen by the dispatcher */
 } gfp_result;
 
 typedef struct gfp_server_stats {

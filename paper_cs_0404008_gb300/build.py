@@ -1,5 +1,6 @@
-"""In-tree build of libgfpdot.so for sm_103a (nvcc, no cmake), and of the
-host sweep library libgfpsweep.so (plain C, the host compiler).
+"""In-tree build of libgfpdot.so for sm_103a (nvcc, no cmake), of the
+host sweep library libgfpsweep.so (plain C, the host compiler) and of the
+measurement library libgfppeaks.so (nvcc).
 
 Each CUDA translation unit under ``csrc/`` is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -lineinfo -O3`` and linked into
@@ -22,6 +23,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgfpdot.so")
 SWEEP_SRC = os.path.join(HERE, "sweep", "gfp_sweep.c")
 SWEEP_LIB = os.path.join(OUT, "libgfpsweep.so")
+PEAKS_SRC = os.path.join(HERE, "peaks", "gfp_peaks.cu")
+PEAKS_LIB = os.path.join(OUT, "libgfppeaks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -52,20 +55,34 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link libgfpdot.so; returns its path."""
-    if not force and up_to_date():
-        return LIB
+SAN_OUT = os.path.join(OUT, "sanitize")
+SAN_LIB = os.path.join(SAN_OUT, "libgfpdot.so")
+SAN_FLAGS = ["-fsanitize=address", "-fsanitize=undefined", "-fno-omit-frame-pointer",
+             "-fno-sanitize-recover=undefined"]
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          sanitize: bool = False) -> str:
+    """Compile and link libgfpdot.so; returns its path.  With sanitize=True the
+    host code is built with AddressSanitizer and UndefinedBehaviorSanitizer
+    into a separate library (_build/sanitize/libgfpdot.so) for host-side test
+    runs (load it with libasan preloaded); device code is unchanged."""
+    out_dir, lib = (SAN_OUT, SAN_LIB) if sanitize else (OUT, LIB)
+    if not force and os.path.exists(lib) and all(os.path.getmtime(d) <= os.path.getmtime(lib)
+                                                 for d in _deps()):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(OUT, exist_ok=True)
+    os.makedirs(out_dir, exist_ok=True)
     common = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-fvisibility=hidden", "-I", os.path.join(ROOT, "include"),
               "-I", CSRC]
+    if sanitize:
+        common += [a for f in SAN_FLAGS for a in ("-Xcompiler", f)]
     if ptxas_info:
         common += ["-Xptxas", "-v"]
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(OUT, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         cmd = common + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -78,14 +95,16 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     with ThreadPoolExecutor(max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         objs = list(ex.map(compile_one, srcs))
     cuda_lib = os.path.join(_cuda_home(nvcc), "lib64")
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
            "-Xlinker", f"-rpath={cuda_lib}", "-lpthread"]
+    if sanitize:
+        cmd += [a for f in SAN_FLAGS for a in ("-Xcompiler", f)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 def build_sweep(force: bool = False) -> str:
@@ -109,7 +128,28 @@ def build_sweep(force: bool = False) -> str:
     return SWEEP_LIB
 
 
+def build_peaks(force: bool = False) -> str:
+    """Compile libgfppeaks.so (the measured ceilings of the rooflines); returns its path."""
+    deps = [PEAKS_SRC, os.path.join(ROOT, "include", "gfppeaks.h"), os.path.abspath(__file__)]
+    if (not force and os.path.exists(PEAKS_LIB)
+            and all(os.path.getmtime(d) <= os.path.getmtime(PEAKS_LIB) for d in deps)):
+        return PEAKS_LIB
+    os.makedirs(OUT, exist_ok=True)
+    nvcc = _nvcc()
+    cuda_lib = os.path.join(_cuda_home(nvcc), "lib64")
+    tmp = PEAKS_LIB + f".{os.getpid()}.tmp"
+    cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
+           "-fvisibility=hidden", "-I", os.path.join(ROOT, "include"), "-shared", "-cudart",
+           "shared", "-o", tmp, PEAKS_SRC, "-Xlinker", f"-rpath={cuda_lib}"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PEAKS_SRC}:\n{r.stderr}")
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
+
+
 if __name__ == "__main__":
     import sys
     print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
     print(build_sweep(force="--force" in sys.argv))
+    print(build_peaks(force="--force" in sys.argv))

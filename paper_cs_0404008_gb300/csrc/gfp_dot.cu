@@ -6,9 +6,10 @@
 // residues, a per-thread unreduced accumulator (Section 3 of the paper),
 // one reduction per thread, a warp-shuffle plus shared-memory combine of the
 // thread residues, one 64-bit atomic add per CTA into the output's slot, and a
-// single final reduction by the last CTA to finish (ticket counter).  The
-// slots and tickets are returned to zero by that last CTA, so the scratch is
-// reusable by the next launch without a memset.
+// single final reduction by the last CTA to finish (found by a ticket counter
+// in the batched kernel, by a CTA count packed into the slot itself in the
+// single-dot kernel).  The last CTA returns slots and tickets to zero, so the
+// scratch is reusable by the next launch without a memset.
 #include "gfp_internal.h"
 
 namespace gfp {
@@ -42,7 +43,20 @@ __device__ __forceinline__ void accumulate_range(Acc &acc, const Mod &m, const u
 #pragma unroll
             for (int u = 0; u < U; ++u) acc.add4(a[u], c[u], m);
         }
-        for (; v < nv; v += T) acc.add4(ld_stream4(xv + v), ld_stream4(yv + v), m);
+        if (v < nv) {
+            // fewer than U loads of each operand remain: issue them together
+            uint4 a[U], c[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (v + u * T < nv) {
+                    a[u] = ld_stream4(xv + v + u * T);
+                    c[u] = ld_stream4(yv + v + u * T);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (v + u * T < nv) acc.add4(a[u], c[u], m);
+        }
         const uint64_t i = b + (nv << 2) + t;   // fewer than 4 tail elements, T >= 4
         if (i < e) acc.add(ld_stream1(x + i), ld_stream1(y + i), m);
     } else {
@@ -99,11 +113,28 @@ __device__ __forceinline__ void combine_and_finish(uint64_t cta_total, const Mod
     }
 }
 
+// Single-dot combine in one atomic: each CTA adds its residue (below 2^32)
+// plus 2^48 to a 64-bit slot, so the low 48 bits collect the residue sum and
+// the high 16 bits count the CTAs (a grid of at most 2^16 - 1 CTAs keeps the
+// sum below 2^48).  The CTA whose add returns a count of grid - 1 holds every
+// other contribution in the returned value: it reduces the total into *out
+// and returns the slot to zero; no fence or second atomic is needed.
+__device__ __forceinline__ void combine_packed(uint64_t cta_total, const Mod &m,
+                                               unsigned long long *slot, uint32_t ctas,
+                                               uint32_t *out)
+{
+    const uint64_t r = reduce64(cta_total, m);
+    const unsigned long long old = atomicAdd(slot, (unsigned long long)r + (1ull << 48));
+    if ((uint32_t)(old >> 48) == ctas - 1) {
+        *slot = 0ull;
+        *out = reduce64((old & ((1ull << 48) - 1)) + r, m);
+    }
+}
+
 template <class Acc>
 __global__ void __launch_bounds__(DOT_THREADS)
     k_dot_single(Mod m, uint64_t k, uint64_t n, const uint32_t *__restrict__ x,
-                 const uint32_t *__restrict__ y, unsigned long long *slot, uint32_t *ticket,
-                 uint32_t *out)
+                 const uint32_t *__restrict__ y, unsigned long long *slot, uint32_t *out)
 {
     // Programmatic dependent launch: let the next kernel of the stream be
     // scheduled now, and wait here until the previous one has finished and
@@ -116,7 +147,7 @@ __global__ void __launch_bounds__(DOT_THREADS)
     const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     accumulate_range<Acc, 4>(acc, m, x, y, 0, n, t, T);
     const uint64_t s = cta_sum(acc.residue(m));
-    if (threadIdx.x == 0) combine_and_finish(s, m, slot, ticket, gridDim.x, out);
+    if (threadIdx.x == 0) combine_packed(s, m, slot, gridDim.x, out);
 }
 
 template <class Acc>
@@ -239,13 +270,14 @@ int dot_single_grid(Repr r, uint64_t n, int sm_count)
     uint64_t want = (n + per_cta - 1) / per_cta;
     const uint64_t cap = (uint64_t)sm_count * occupancy_for(r);
     if (want < 1) want = 1;
-    return (int)(want < cap ? want : cap);
+    want = want < cap ? want : cap;
+    return (int)(want < 65535 ? want : 65535);   // the packed combine counts CTAs in 16 bits
 }
 
 template <class Acc>
 static cudaError_t launch_single_pdl(const Mod &m, uint64_t k, uint64_t n, const uint32_t *x,
-                                     const uint32_t *y, unsigned long long *slot, uint32_t *ticket,
-                                     uint32_t *out, int grid, cudaStream_t s)
+                                     const uint32_t *y, unsigned long long *slot, uint32_t *out,
+                                     int grid, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -257,21 +289,21 @@ static cudaError_t launch_single_pdl(const Mod &m, uint64_t k, uint64_t n, const
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_dot_single<Acc>, m, k, n, x, y, slot, ticket, out);
+    return cudaLaunchKernelEx(&cfg, k_dot_single<Acc>, m, k, n, x, y, slot, out);
 }
 
 cudaError_t launch_dot_single(Repr r, const Mod &m, uint64_t k, uint64_t n, const uint32_t *x,
-                              const uint32_t *y, unsigned long long *slot, uint32_t *ticket,
-                              uint32_t *out, int grid, cudaStream_t s)
+                              const uint32_t *y, unsigned long long *slot, uint32_t *out, int grid,
+                              cudaStream_t s)
 {
     cudaError_t e;
     switch (r) {
-    case U64_BLOCK: e = launch_single_pdl<AccBlock>(m, k, n, x, y, slot, ticket, out, grid, s); break;
-    case U64_CARRY: e = launch_single_pdl<AccCarry>(m, k, n, x, y, slot, ticket, out, grid, s); break;
-    case FP64: e = launch_single_pdl<AccF64>(m, k, n, x, y, slot, ticket, out, grid, s); break;
-    case CENTERED: e = launch_single_pdl<AccCentered>(m, k, n, x, y, slot, ticket, out, grid, s); break;
-    case MONTGOMERY: e = launch_single_pdl<AccMontgomery>(m, k, n, x, y, slot, ticket, out, grid, s); break;
-    default: e = launch_single_pdl<AccPerTerm>(m, k, n, x, y, slot, ticket, out, grid, s); break;
+    case U64_BLOCK: e = launch_single_pdl<AccBlock>(m, k, n, x, y, slot, out, grid, s); break;
+    case U64_CARRY: e = launch_single_pdl<AccCarry>(m, k, n, x, y, slot, out, grid, s); break;
+    case FP64: e = launch_single_pdl<AccF64>(m, k, n, x, y, slot, out, grid, s); break;
+    case CENTERED: e = launch_single_pdl<AccCentered>(m, k, n, x, y, slot, out, grid, s); break;
+    case MONTGOMERY: e = launch_single_pdl<AccMontgomery>(m, k, n, x, y, slot, out, grid, s); break;
+    default: e = launch_single_pdl<AccPerTerm>(m, k, n, x, y, slot, out, grid, s); break;
     }
     return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -508,6 +508,7 @@ extern "C" {
 
 GFP_API gfp_status gfp_gfq_find_primitive(uint32_t p, uint32_t k, uint32_t *f)
 {
+    GFP_TRACE();
     uint32_t q;
     if (!f || !gfq::order_params(p, k, q)) return GFP_ERR_INVALID;
     std::vector<uint32_t> expv, logv;
@@ -529,6 +530,7 @@ GFP_API gfp_status gfp_gfq_find_primitive(uint32_t p, uint32_t k, uint32_t *f)
 
 GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint32_t *f, gfp_gfq **out)
 {
+    GFP_TRACE();
     uint32_t q;
     if (!out || !f || !gfq::order_params(p, k, q)) return GFP_ERR_INVALID;
     *out = nullptr;
@@ -626,6 +628,7 @@ GFP_API gfp_status gfp_gfq_create(int device, uint32_t p, uint32_t k, const uint
 
 GFP_API gfp_status gfp_gfq_destroy(gfp_gfq *fq)
 {
+    GFP_TRACE();
     if (!fq) return GFP_ERR_INVALID;
     cudaSetDevice(fq->device);
     cudaFree(fq->d_zech);
@@ -659,6 +662,7 @@ static int conv_grid(const gfp_gfq *fq, uint64_t n)
 GFP_API gfp_status gfp_gfq_to_log(gfp_gfq *fq, uint64_t n, const uint32_t *values, uint16_t *codes,
                                   void *stream)
 {
+    GFP_TRACE();
     if (!fq || (n && (!values || !codes))) return GFP_ERR_INVALID;
     if (n == 0) return GFP_OK;
     GFQ_TRY(cudaSetDevice(fq->device));
@@ -671,6 +675,7 @@ GFP_API gfp_status gfp_gfq_to_log(gfp_gfq *fq, uint64_t n, const uint32_t *value
 GFP_API gfp_status gfp_gfq_from_log(gfp_gfq *fq, uint64_t n, const uint16_t *codes, uint32_t *values,
                                     void *stream)
 {
+    GFP_TRACE();
     if (!fq || (n && (!values || !codes))) return GFP_ERR_INVALID;
     if (n == 0) return GFP_OK;
     GFQ_TRY(cudaSetDevice(fq->device));
@@ -683,6 +688,7 @@ GFP_API gfp_status gfp_gfq_from_log(gfp_gfq *fq, uint64_t n, const uint16_t *cod
 GFP_API gfp_status gfp_gfq_dot(gfp_gfq *fq, uint64_t n, const uint16_t *x, const uint16_t *y, uint16_t *out,
                                void *stream)
 {
+    GFP_TRACE();
     if (!fq || !out || (n && (!x || !y))) return GFP_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     GFQ_TRY(cudaSetDevice(fq->device));
@@ -716,6 +722,7 @@ GFP_API gfp_status gfp_gfq_dot(gfp_gfq *fq, uint64_t n, const uint16_t *x, const
 
 GFP_API gfp_status gfp_gfq_check(gfp_gfq *fq)
 {
+    GFP_TRACE();
     if (!fq) return GFP_ERR_INVALID;
     GFQ_TRY(cudaSetDevice(fq->device));
     GFQ_TRY(cudaDeviceSynchronize());

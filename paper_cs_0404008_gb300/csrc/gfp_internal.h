@@ -9,10 +9,24 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gfp_arith.cuh"
 #include "../../include/gfpdot.h"
 
 namespace gfp {
+
+// NVTX range spanning one entry point, named after it, so that a profiler
+// timeline (Nsight Systems, ncu --nvtx) shows each library call around the
+// kernels it launched.  Without an attached tool the push and pop return at
+// once (NVTX v3 is header-only and loads nothing unless a tool asks).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+#define GFP_TRACE() ::gfp::TraceRange gfp_trace_range_(__func__)
 
 // One pair of a batch as the persistent kernel sees it (64 bytes).
 struct DevPair {
@@ -61,8 +75,8 @@ struct BatchScratch {
 
 // Kernel launchers (gfp_dot.cu, gfp_matvec.cu).
 cudaError_t launch_dot_single(Repr r, const Mod &m, uint64_t k, uint64_t n, const uint32_t *x,
-                              const uint32_t *y, unsigned long long *slot, uint32_t *ticket,
-                              uint32_t *out, int grid, cudaStream_t s);
+                              const uint32_t *y, unsigned long long *slot, uint32_t *out, int grid,
+                              cudaStream_t s);
 int dot_single_grid(Repr r, uint64_t n, int sm_count);
 cudaError_t launch_dot_batched(const DevPair *pairs, const DevPairAux *aux, const DevUnit *units,
                                uint32_t n_units, BatchScratch sc, uint32_t *out, int grid,
@@ -124,6 +138,12 @@ cudaError_t launch_block_csr(Repr r, const Mod &mod, uint64_t kbound, uint64_t m
                              const uint32_t *row_ptr, const uint32_t *col, const uint32_t *val,
                              const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc,
                              int sm_count, cudaStream_t s);
+// The 16-bit gather form for p <= 65536 (B packed into Bh, k * nb uint16).
+bool csr_h16_eligible(Repr r, uint32_t p, uint64_t k, uint64_t nb);
+cudaError_t launch_block_csr_h16(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
+                                 const uint32_t *row_ptr, const uint32_t *col, const uint32_t *val,
+                                 const uint32_t *B, uint64_t ldb, uint16_t *Bh, uint32_t *C,
+                                 uint64_t ldc, int sm_count, cudaStream_t s);
 
 }  // namespace gfp
 
@@ -143,9 +163,8 @@ struct gfp_ctx {
     std::atomic<uint64_t> launches{0};
     std::mutex mu;
 
-    // single-dot scratch ring
+    // single-dot scratch ring: one packed (residue sum, CTA count) word per slot
     unsigned long long *ring_slots = nullptr;
-    uint32_t *ring_tickets = nullptr;
     uint32_t ring_size = 1024;
     std::atomic<uint32_t> ring_pos{0};
 
@@ -170,6 +189,9 @@ struct gfp_ctx {
     // flag); zero outside calls except the B image; grown on demand
     void *blk_ws = nullptr;
     size_t blk_ws_bytes = 0;
+    // sparse-row product: B packed to 16 bits (p <= 65536); grown on demand
+    uint16_t *csr_b16 = nullptr;
+    size_t csr_b16_bytes = 0;
     uint64_t blk_m = 0, blk_k = 0, blk_nb = 0;   // shape whose error flag is live
 
     // tuned plan: (p, lg_n) -> entry

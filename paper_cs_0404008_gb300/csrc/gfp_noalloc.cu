@@ -48,6 +48,12 @@ NoAllocScratch *d_addr[NA_MAX_DEVICES];
 int d_sms[NA_MAX_DEVICES];
 std::mutex na_mutex;
 
+gfp_status fail(cudaError_t e)
+{
+    note_cuda_error(e);
+    return GFP_ERR_CUDA;
+}
+
 double unit_cost(const DevUnit &u, const DevPairAux *aux)
 {
     const uint32_t r = aux[u.pair].repr;
@@ -67,23 +73,27 @@ extern "C" GFP_API gfp_status gfp_dot_batched_noalloc(const gfp_dot_desc *d, uin
     if (count == 0) return GFP_OK;
     if (count > NA_MAX_PAIRS) return GFP_ERR_INVALID;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return GFP_ERR_CUDA;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return fail(e0);
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return GFP_ERR_CUDA;
 
     std::lock_guard<std::mutex> g(na_mutex);
     // set-up, once per device, with that device current: the device address
     // of the scratch array (its host-side name is only a stand-in)
     if (!d_addr[dev]) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GFP_ERR_CUDA;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
         int sms = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return GFP_ERR_CUDA;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return fail(e);
         d_sms[dev] = sms;
         d_addr[dev] = (NoAllocScratch *)p;
     }
     NoAllocScratch *dsc = d_addr[dev];
 
-    // descriptors and work list in the static host staging
+    // first pass: check every descriptor and count the work units, writing
+    // nothing, so a refused batch leaves the staging and the device untouched
     uint64_t nu = 0;
     for (uint64_t j = 0; j < count; ++j) {
         const gfp_dot_desc &q = d[j];
@@ -95,6 +105,16 @@ extern "C" GFP_API gfp_status gfp_dot_batched_noalloc(const gfp_dot_desc *d, uin
             return GFP_ERR_UNSUPPORTED;
         const uint64_t units = q.n ? (q.n + NA_CHUNK - 1) / NA_CHUNK : 1;
         if (units > NA_MAX_UNITS - nu) return GFP_ERR_INVALID;   // work list would not fit
+        nu += units;
+    }
+
+    // second pass: descriptors and work list in the static host staging
+    uint64_t w = 0;
+    for (uint64_t j = 0; j < count; ++j) {
+        const gfp_dot_desc &q = d[j];
+        uint32_t r = q.repr;
+        if (r == GFP_REPR_AUTO) r = gfp_choose_repr(nullptr, q.p, q.n);
+        const uint64_t units = q.n ? (q.n + NA_CHUNK - 1) / NA_CHUNK : 1;
         DevPair &pr = h_stage.pairs[j];
         pr.x = q.x;
         pr.y = q.y;
@@ -104,37 +124,44 @@ extern "C" GFP_API gfp_status gfp_dot_batched_noalloc(const gfp_dot_desc *d, uin
         h_stage.aux[j].repr = r;
         h_stage.aux[j].units = (uint32_t)units;
         if (q.n == 0) {
-            h_stage.units[nu++] = DevUnit{0, 0, (uint32_t)j, 0};
+            h_stage.units[w++] = DevUnit{0, 0, (uint32_t)j, 0};
         } else {
             for (uint64_t b = 0; b < q.n; b += NA_CHUNK)
-                h_stage.units[nu++] = DevUnit{b, std::min<uint64_t>(q.n, b + NA_CHUNK), (uint32_t)j, 0};
+                h_stage.units[w++] = DevUnit{b, std::min<uint64_t>(q.n, b + NA_CHUNK), (uint32_t)j, 0};
         }
     }
-    std::stable_sort(h_stage.units, h_stage.units + nu, [](const DevUnit &a, const DevUnit &b) {
-        return unit_cost(a, h_stage.aux) > unit_cost(b, h_stage.aux);
+    // largest units first; ties in (pair, start) order so the order is total.
+    // std::sort sorts in place (std::stable_sort may take a heap buffer).
+    std::sort(h_stage.units, h_stage.units + nu, [](const DevUnit &a, const DevUnit &b) {
+        const double ca = unit_cost(a, h_stage.aux), cb = unit_cost(b, h_stage.aux);
+        if (ca != cb) return ca > cb;
+        if (a.pair != b.pair) return a.pair < b.pair;
+        return a.begin < b.begin;
     });
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // pageable copies: the staging may be reused as soon as these return
-    if (cudaMemcpyAsync(dsc->pairs, h_stage.pairs, count * sizeof(DevPair), cudaMemcpyHostToDevice,
-                        s) != cudaSuccess ||
-        cudaMemcpyAsync(dsc->aux, h_stage.aux, count * sizeof(DevPairAux), cudaMemcpyHostToDevice,
-                        s) != cudaSuccess ||
-        cudaMemcpyAsync(dsc->units, h_stage.units, nu * sizeof(DevUnit), cudaMemcpyHostToDevice,
-                        s) != cudaSuccess)
-        return GFP_ERR_CUDA;
+    cudaError_t e = cudaMemcpyAsync(dsc->pairs, h_stage.pairs, count * sizeof(DevPair),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dsc->aux, h_stage.aux, count * sizeof(DevPairAux),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dsc->units, h_stage.units, nu * sizeof(DevUnit),
+                            cudaMemcpyHostToDevice, s);
     // clear what must start at zero (the kernel also leaves it zero, but a
     // previous launch that failed would not have)
-    if (cudaMemsetAsync(dsc->slots, 0, count * sizeof(unsigned long long), s) != cudaSuccess ||
-        cudaMemsetAsync(dsc->tickets, 0, count * sizeof(uint32_t), s) != cudaSuccess ||
-        cudaMemsetAsync(dsc->ctr, 0, sizeof(dsc->ctr), s) != cudaSuccess)
-        return GFP_ERR_CUDA;
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(dsc->slots, 0, count * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dsc->tickets, 0, count * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dsc->ctr, 0, sizeof(dsc->ctr), s);
+    if (e != cudaSuccess) return fail(e);
     BatchScratch sc;
     sc.slots = dsc->slots;
     sc.tickets = dsc->tickets;
     sc.ctr = dsc->ctr;
-    if (launch_dot_batched(dsc->pairs, dsc->aux, dsc->units, (uint32_t)nu, sc, out,
-                           dot_batched_grid(d_sms[dev]), s) != cudaSuccess)
-        return GFP_ERR_CUDA;
+    e = launch_dot_batched(dsc->pairs, dsc->aux, dsc->units, (uint32_t)nu, sc, out,
+                           dot_batched_grid(d_sms[dev]), s);
+    if (e != cudaSuccess) return fail(e);
     return GFP_OK;
 }

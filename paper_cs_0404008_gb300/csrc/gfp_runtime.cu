@@ -399,6 +399,7 @@ GFP_API gfp_status gfp_plan_load(gfp_ctx *ctx, const char *path);   // gfp_tune.
 
 GFP_API gfp_status gfp_context_create(int device, gfp_ctx **out)
 {
+    GFP_TRACE();
     if (!out) return GFP_ERR_INVALID;
     *out = nullptr;
     int ndev = 0;
@@ -413,7 +414,7 @@ GFP_API gfp_status gfp_context_create(int device, gfp_ctx **out)
         delete c;
         return GFP_ERR_CUDA;
     }
-    const size_t ring_bytes = (size_t)c->ring_size * (sizeof(unsigned long long) + 4);
+    const size_t ring_bytes = (size_t)c->ring_size * sizeof(unsigned long long);
     void *mem = nullptr;
     if (cudaMalloc(&mem, ring_bytes + 256) != cudaSuccess) {
         delete c;
@@ -421,7 +422,6 @@ GFP_API gfp_status gfp_context_create(int device, gfp_ctx **out)
     }
     cudaMemset(mem, 0, ring_bytes + 256);
     c->ring_slots = (unsigned long long *)mem;
-    c->ring_tickets = (uint32_t *)((char *)mem + (size_t)c->ring_size * 8);
     c->d_flag = (uint32_t *)((char *)mem + ring_bytes);
     if (cudaDeviceSynchronize() != cudaSuccess) {
         cudaFree(mem);
@@ -440,6 +440,7 @@ GFP_API gfp_status gfp_context_create(int device, gfp_ctx **out)
 
 GFP_API gfp_status gfp_context_destroy(gfp_ctx *ctx)
 {
+    GFP_TRACE();
     if (!ctx) return GFP_ERR_INVALID;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
@@ -456,12 +457,14 @@ GFP_API gfp_status gfp_context_destroy(gfp_ctx *ctx)
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->stage_out) cudaFree(ctx->stage_out);
     if (ctx->blk_ws) cudaFree(ctx->blk_ws);
+    if (ctx->csr_b16) cudaFree(ctx->csr_b16);
     delete ctx;
     return GFP_OK;
 }
 
 GFP_API gfp_status gfp_set_repr(gfp_ctx *ctx, gfp_repr repr)
 {
+    GFP_TRACE();
     if (!ctx || repr < GFP_REPR_AUTO || repr >= GFP_REPR_COUNT_) return GFP_ERR_INVALID;
     ctx->forced = repr;
     return GFP_OK;
@@ -469,6 +472,7 @@ GFP_API gfp_status gfp_set_repr(gfp_ctx *ctx, gfp_repr repr)
 
 GFP_API gfp_status gfp_set_validate(gfp_ctx *ctx, int on)
 {
+    GFP_TRACE();
     if (!ctx) return GFP_ERR_INVALID;
     ctx->validate = on != 0;
     return GFP_OK;
@@ -479,6 +483,7 @@ GFP_API uint64_t gfp_launch_count(const gfp_ctx *ctx) { return ctx ? ctx->launch
 GFP_API gfp_status gfp_dot(gfp_ctx *ctx, uint32_t p, uint64_t n, const uint32_t *x,
                            const uint32_t *y, uint32_t *out, void *stream)
 {
+    GFP_TRACE();
     if (!ctx || p < 2 || !out || (n && (!x || !y))) return GFP_ERR_INVALID;
     if ((((uintptr_t)x) | ((uintptr_t)y) | ((uintptr_t)out)) & 3u) return GFP_ERR_INVALID;
     Repr r;
@@ -492,7 +497,7 @@ GFP_API gfp_status gfp_dot(gfp_ctx *ctx, uint32_t p, uint64_t n, const uint32_t 
     const uint32_t slot = ctx->ring_pos.fetch_add(1) % ctx->ring_size;
     const int grid = dot_single_grid(r, n, ctx->sm_count);
     GFP_CUDA_TRY(launch_dot_single(r, make_mod(p), k_for(r, p), n, x, y, ctx->ring_slots + slot,
-                                   ctx->ring_tickets + slot, out, grid, s));
+                                   out, grid, s));
     ctx->launches++;
     return GFP_OK;
 }
@@ -500,6 +505,7 @@ GFP_API gfp_status gfp_dot(gfp_ctx *ctx, uint32_t p, uint64_t n, const uint32_t 
 GFP_API gfp_status gfp_batch_plan_create(gfp_ctx *ctx, const gfp_dot_desc *d, uint64_t count,
                                          gfp_batch_plan **out)
 {
+    GFP_TRACE();
     if (!ctx || !out || (count && !d)) return GFP_ERR_INVALID;
     *out = nullptr;
     HostBatch hb;
@@ -537,6 +543,7 @@ GFP_API gfp_status gfp_batch_plan_create(gfp_ctx *ctx, const gfp_dot_desc *d, ui
 
 GFP_API gfp_status gfp_batch_plan_exec(gfp_batch_plan *pl, uint32_t *out, void *stream)
 {
+    GFP_TRACE();
     if (!pl || (pl->count && !out)) return GFP_ERR_INVALID;
     if (pl->count == 0) return GFP_OK;
     GFP_CUDA_TRY(launch_dot_batched(pl->pairs, pl->aux, pl->units, (uint32_t)pl->n_units, pl->sc,
@@ -547,6 +554,7 @@ GFP_API gfp_status gfp_batch_plan_exec(gfp_batch_plan *pl, uint32_t *out, void *
 
 GFP_API gfp_status gfp_batch_plan_info(const gfp_batch_plan *pl, uint64_t *units, uint64_t *bytes)
 {
+    GFP_TRACE();
     if (!pl) return GFP_ERR_INVALID;
     if (units) *units = pl->n_units;
     if (bytes) *bytes = pl->bytes;
@@ -555,6 +563,7 @@ GFP_API gfp_status gfp_batch_plan_info(const gfp_batch_plan *pl, uint64_t *units
 
 GFP_API gfp_status gfp_batch_plan_destroy(gfp_batch_plan *pl)
 {
+    GFP_TRACE();
     if (!pl) return GFP_ERR_INVALID;
     cudaFree(pl->mem);
     delete pl;
@@ -610,6 +619,7 @@ static gfp_status batched_oneshot(gfp_ctx *ctx, const gfp_dot_desc *d, uint64_t 
 GFP_API gfp_status gfp_dot_batched(gfp_ctx *ctx, const gfp_dot_desc *d, uint64_t count,
                                    uint32_t *out, void *stream)
 {
+    GFP_TRACE();
     if (!ctx || (count && (!d || !out))) return GFP_ERR_INVALID;
     if (count == 0) return GFP_OK;
     std::lock_guard<std::mutex> g(ctx->mu);
@@ -621,6 +631,7 @@ GFP_API gfp_status gfp_dot_batched_host(gfp_ctx *ctx, uint64_t count, const uint
                                         const uint32_t *x_host, const uint32_t *y_host,
                                         uint64_t total, uint32_t *out_host, void *stream)
 {
+    GFP_TRACE();
     if (!ctx || (count && (!p || !n || !off || !out_host))) return GFP_ERR_INVALID;
     if (count == 0) return GFP_OK;
     if (total && (!x_host || !y_host)) return GFP_ERR_INVALID;
@@ -683,6 +694,7 @@ GFP_API gfp_status gfp_matvec(gfp_ctx *ctx, uint32_t p, uint64_t rows, uint64_t 
                               const uint32_t *A, uint64_t lda, const uint32_t *x, uint32_t *y,
                               void *stream)
 {
+    GFP_TRACE();
     if (!ctx || p < 2 || lda < cols || (rows && !y) || (rows && cols && (!A || !x)))
         return GFP_ERR_INVALID;
     if ((((uintptr_t)A) | ((uintptr_t)x) | ((uintptr_t)y)) & 3u) return GFP_ERR_INVALID;
@@ -705,6 +717,7 @@ GFP_API gfp_status gfp_matvec_iterate(gfp_ctx *ctx, uint32_t p, uint64_t n, cons
                                       uint64_t lda, const uint32_t *x0, uint32_t *Y,
                                       uint32_t iters, void *stream)
 {
+    GFP_TRACE();
     if (!ctx || p < 2 || lda < n || (n && (!A || !x0 || !Y))) return GFP_ERR_INVALID;
     if ((((uintptr_t)A) | ((uintptr_t)x0) | ((uintptr_t)Y)) & 3u) return GFP_ERR_INVALID;
     if (n == 0 || iters == 0) return GFP_OK;
@@ -756,6 +769,7 @@ GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64
                                     const uint32_t *A, uint64_t lda, const uint32_t *B,
                                     uint64_t ldb, uint32_t *C, uint64_t ldc, void *stream)
 {
+    GFP_TRACE();
     if (!ctx || p < 2 || lda < k || ldb < nb || ldc < nb) return GFP_ERR_INVALID;
     if ((m && nb && !C) || (m && k && !A) || (k && nb && !B)) return GFP_ERR_INVALID;
     if ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 3u) return GFP_ERR_INVALID;
@@ -843,6 +857,7 @@ GFP_API gfp_status gfp_matmul_block_csr(gfp_ctx *ctx, uint32_t p, uint64_t m, ui
                                         const uint32_t *val, const uint32_t *B, uint64_t ldb,
                                         uint32_t *C, uint64_t ldc, void *stream)
 {
+    GFP_TRACE();
     if (!ctx || p < 2 || ldb < nb || ldc < nb) return GFP_ERR_INVALID;
     if (m && (!row_ptr || (nb && !C))) return GFP_ERR_INVALID;
     if ((((uintptr_t)row_ptr) | ((uintptr_t)col) | ((uintptr_t)val) | ((uintptr_t)B) |
@@ -872,6 +887,22 @@ GFP_API gfp_status gfp_matmul_block_csr(gfp_ctx *ctx, uint32_t p, uint64_t m, ui
         GFP_CUDA_TRY(cudaMemset2DAsync(C, ldc * 4, 0, nb * 4, m, s));
         return GFP_OK;
     }
+    if (csr_h16_eligible(r, p, k, nb)) {
+        const size_t need = (size_t)k * nb * 2;
+        if (ctx->csr_b16_bytes < need) {
+            if (ctx->csr_b16) cudaFree(ctx->csr_b16);
+            ctx->csr_b16 = nullptr;
+            ctx->csr_b16_bytes = 0;
+            void *mem = nullptr;
+            if (cudaMalloc(&mem, need) != cudaSuccess) return GFP_ERR_NOMEM;
+            ctx->csr_b16 = (uint16_t *)mem;
+            ctx->csr_b16_bytes = need;
+        }
+        GFP_CUDA_TRY(launch_block_csr_h16(make_mod(p), m, k, nb, row_ptr, col, val, B, ldb,
+                                          ctx->csr_b16, C, ldc, ctx->sm_count, s));
+        ctx->launches += 2;
+        return GFP_OK;
+    }
     GFP_CUDA_TRY(launch_block_csr(r, make_mod(p), k_for(r, p), m, k, nb, row_ptr, col, val, B, ldb,
                                   C, ldc, ctx->sm_count, s));
     ctx->launches++;
@@ -896,6 +927,7 @@ GFP_API gfp_status gfp_context_check(gfp_ctx *ctx)
 
 GFP_API gfp_status gfp_wait_selftest(uint64_t limit_ns, void *stream)
 {
+    GFP_TRACE();
     if (limit_ns < 1000000ull || limit_ns > 2000000000ull) return GFP_ERR_INVALID;
     uint32_t bits = 0;
     GFP_CUDA_TRY(wait_selftest(limit_ns, as_stream(stream), &bits));
@@ -906,6 +938,7 @@ GFP_API gfp_status gfp_matvec_sequence(gfp_ctx *ctx, uint32_t p, uint64_t n, con
                                        uint64_t lda, const uint32_t *x0, const uint32_t *u,
                                        uint32_t iters, uint32_t *seq, uint32_t *Y, void *stream)
 {
+    GFP_TRACE();
     if (!ctx || p < 2 || lda < n || !seq || (n && (!A || !x0 || !u))) return GFP_ERR_INVALID;
     if ((((uintptr_t)A) | ((uintptr_t)x0) | ((uintptr_t)u) | ((uintptr_t)seq) | ((uintptr_t)Y)) & 3u)
         return GFP_ERR_INVALID;
@@ -950,7 +983,7 @@ GFP_API gfp_status gfp_matvec_sequence(gfp_ctx *ctx, uint32_t p, uint64_t n, con
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess)
-            e = launch_dot_single(r, m, k, n, u, x0, ctx->seq_slots, ctx->seq_tickets, seq,
+            e = launch_dot_single(r, m, k, n, u, x0, ctx->seq_slots, seq,
                                   dot_single_grid(r, n, ctx->sm_count), cs);
         for (uint32_t t = 1; e == cudaSuccess && t <= iters; ++t) {
             const uint32_t *xin = (t == 1) ? x0
@@ -979,6 +1012,7 @@ GFP_API gfp_status gfp_matvec_sequence(gfp_ctx *ctx, uint32_t p, uint64_t n, con
 GFP_API gfp_status gfp_fill_uniform(uint32_t p, uint64_t seed, uint64_t stream_id,
                                     uint64_t offset, uint64_t n, uint32_t *out, void *stream)
 {
+    GFP_TRACE();
     if (p < 2 || (n && !out)) return GFP_ERR_INVALID;
     GFP_CUDA_TRY(launch_fill_uniform(p, seed, stream_id, offset, n, out, as_stream(stream)));
     return GFP_OK;

@@ -423,6 +423,8 @@ bool gfp_server::admit_and_launch()
                     cudaEventRecord(L.ev, streams[L.stream]) != cudaSuccess)
                     L.status = GFP_ERR_CUDA;
             }
+            const uint64_t t_q = now_ns();   // every launch of the batch is enqueued
+            for (uint64_t tk : dots) jobs.at(tk).res.t_start_ns = t_q;
         }
         running.push_back(std::move(L));
     }
@@ -439,6 +441,7 @@ bool gfp_server::admit_and_launch()
             L.status = launch_one(tk, L);
             if (L.status == GFP_OK && cudaEventRecord(L.ev, streams[L.stream]) != cudaSuccess)
                 L.status = GFP_ERR_CUDA;
+            r.res.t_start_ns = now_ns();   // the job's launches are enqueued
         }
         running.push_back(std::move(L));
     }
@@ -466,6 +469,7 @@ extern "C" {
 
 GFP_API gfp_status gfp_server_create(const gfp_server_cfg *cfg, gfp_server **out)
 {
+    GFP_TRACE();
     if (!cfg || !out) return GFP_ERR_INVALID;
     *out = nullptr;
     gfp_server *s = new (std::nothrow) gfp_server();
@@ -519,6 +523,7 @@ GFP_API gfp_status gfp_server_create(const gfp_server_cfg *cfg, gfp_server **out
 
 GFP_API gfp_status gfp_server_destroy(gfp_server *s)
 {
+    GFP_TRACE();
     if (!s) return GFP_ERR_INVALID;
     {
         std::lock_guard<std::mutex> g(s->mu);
@@ -561,6 +566,7 @@ GFP_API gfp_status gfp_server_destroy(gfp_server *s)
 GFP_API gfp_status gfp_register_matrix(gfp_server *s, uint32_t p, uint64_t rows, uint64_t cols,
                                        const uint32_t *dev, uint64_t seed, uint64_t *handle)
 {
+    GFP_TRACE();
     if (!s || !handle || p < 2 || rows == 0 || cols == 0) return GFP_ERR_INVALID;
     if (dev && (((uintptr_t)dev) & 3u)) return GFP_ERR_INVALID;
     Matrix M{p, rows, cols, dev, nullptr, cols};
@@ -587,6 +593,7 @@ GFP_API gfp_status gfp_register_matrix(gfp_server *s, uint32_t p, uint64_t rows,
 
 GFP_API gfp_status gfp_submit(gfp_server *s, const gfp_job *job, uint64_t *ticket)
 {
+    GFP_TRACE();
     if (!s || !job || !ticket) return GFP_ERR_INVALID;
     const gfp_job &j = *job;
     if (j.kind > GFP_JOB_BLOCK || j.p < 2) return GFP_ERR_INVALID;
@@ -636,6 +643,7 @@ GFP_API gfp_status gfp_poll(gfp_server *s, uint64_t ticket, gfp_result *res)
 
 GFP_API gfp_status gfp_wait(gfp_server *s, uint64_t ticket, uint64_t timeout_us, gfp_result *res)
 {
+    GFP_TRACE();
     if (!s) return GFP_ERR_INVALID;
     std::unique_lock<std::mutex> lk(s->mu);
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us);
@@ -659,6 +667,7 @@ GFP_API gfp_status gfp_wait(gfp_server *s, uint64_t ticket, uint64_t timeout_us,
 
 GFP_API gfp_status gfp_result_copy(gfp_server *s, uint64_t ticket, uint32_t *host, uint64_t count)
 {
+    GFP_TRACE();
     if (!s || (count && !host)) return GFP_ERR_INVALID;
     uint64_t off;
     {
@@ -680,6 +689,7 @@ GFP_API gfp_status gfp_result_copy(gfp_server *s, uint64_t ticket, uint32_t *hos
 
 GFP_API gfp_status gfp_release(gfp_server *s, uint64_t ticket)
 {
+    GFP_TRACE();
     if (!s) return GFP_ERR_INVALID;
     std::lock_guard<std::mutex> g(s->mu);
     auto it = s->jobs.find(ticket);

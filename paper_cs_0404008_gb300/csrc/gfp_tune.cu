@@ -58,6 +58,7 @@ extern "C" {
 
 GFP_API gfp_status gfp_plan_load(gfp_ctx *ctx, const char *path)
 {
+    GFP_TRACE();
     if (!ctx || !path) return GFP_ERR_INVALID;
     FILE *f = fopen(path, "rb");
     if (!f) return GFP_ERR_INVALID;
@@ -76,6 +77,7 @@ GFP_API gfp_status gfp_plan_load(gfp_ctx *ctx, const char *path)
 
 GFP_API gfp_status gfp_plan_save(const gfp_ctx *ctx, const char *path)
 {
+    GFP_TRACE();
     if (!ctx || !path) return GFP_ERR_INVALID;
     FILE *f = fopen(path, "wb");
     if (!f) return GFP_ERR_INVALID;
@@ -97,6 +99,7 @@ GFP_API uint64_t gfp_plan_size(const gfp_ctx *ctx) { return ctx ? ctx->plan.size
 GFP_API gfp_status gfp_tune(gfp_ctx *ctx, const uint32_t *primes, uint32_t nprimes,
                             uint32_t lg_lo, uint32_t lg_hi, const char *plan_path)
 {
+    GFP_TRACE();
     static const uint32_t kDefault[] = {32749u, 65521u, 67108859u, 2147483647u, 4294967291u};
     if (!ctx || lg_lo > lg_hi || lg_hi > 26) return GFP_ERR_INVALID;
     if (!primes || nprimes == 0) {

@@ -148,15 +148,20 @@ _lib = None
 
 
 def load(auto_build: bool = True):
-    """Load the in-tree libgfpdot.so (building it first when stale)."""
+    """Load the in-tree libgfpdot.so (building it first when stale).  The
+    environment variable GFPDOT_SANITIZED=1 selects the host-sanitized build
+    instead (AddressSanitizer and UndefinedBehaviorSanitizer in the host code;
+    the process must have libasan preloaded)."""
     global _lib
     if _lib is None:
+        sanitized = os.environ.get("GFPDOT_SANITIZED") == "1"
+        path = _build.SAN_LIB if sanitized else _build.LIB
         if auto_build:
-            _build.build()
-        if not os.path.exists(_build.LIB):
-            raise RuntimeError(f"libgfpdot.so is missing at {_build.LIB}: build it with "
+            _build.build(sanitize=sanitized)
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgfpdot.so is missing at {path}: build it with "
                                "paper_cs_0404008_gb300.build.build()")
-        lib = ctypes.CDLL(_build.LIB)
+        lib = ctypes.CDLL(path)
         for name, (res, args) in _SIGS.items():
             f = getattr(lib, name)
             f.restype = res
@@ -166,7 +171,7 @@ def load(auto_build: bool = True):
 
 
 def lib_path() -> str:
-    return _build.LIB
+    return _build.SAN_LIB if os.environ.get("GFPDOT_SANITIZED") == "1" else _build.LIB
 
 
 def declared_symbols() -> list[str]:

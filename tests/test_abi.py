@@ -79,3 +79,25 @@ def test_gpu_library_does_not_contain_the_sweep(lib):
     out = subprocess.run(["nm", "-D", "--defined-only", lib.lib_path()], capture_output=True,
                          text=True).stdout
     assert "gfp_sweep_" not in out
+
+
+def test_peaks_library_exports_its_header():
+    from paper_cs_0404008_gb300 import build
+    path = build.build_peaks()
+    txt = open(os.path.join(ROOT, "include", "gfppeaks.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    syms = set(re.findall(r"\b(gfp_peak_\w+)\s*\(", txt))
+    assert syms == {"gfp_peak_measure", "gfp_peak_name"}
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert {s for s in exported if s.startswith("gfp_")} == syms
+
+
+def test_peaks_refuses_bad_arguments_without_a_gpu():
+    from paper_cs_0404008_gb300 import peaks
+    so = peaks.lib()
+    r = peaks.gfp_peak_result()
+    assert so.gfp_peak_measure(99, 0, 1, ctypes.byref(r)) == -1
+    assert so.gfp_peak_measure(0, 1 << 30, 0, ctypes.byref(r)) == -1
+    assert so.gfp_peak_measure(0, 16, 1, ctypes.byref(r)) == -1
+    assert so.gfp_peak_name(0) == b"read_hbm" and so.gfp_peak_name(7) is None

@@ -1,7 +1,7 @@
 """Full-size workloads against the oracle: the 4096-pair batched dot workload
 (every result), and the 32768 x 32768 Wiedemann iteration over GF(2^31-1)
-(first iteration row by row, every iteration by Freivalds' check, sampled rows
-of every iteration)."""
+(every element of all 64 iterations against the oracle's matrix-vector
+product of the previous iterate, plus Freivalds' check per iteration)."""
 import numpy as np
 import pytest
 import torch
@@ -44,19 +44,16 @@ def test_wiedemann_iteration_full(lib, ctx):
     torch.cuda.synchronize()
     Yh = host(Y).reshape(iters, n)
     del Ad
-    # iteration 1, every row
-    assert np.array_equal(Yh[0], oracle.matvec(p, A, x0))
     # Freivalds per iteration: u^T (A y_{t-1}) = (u^T A) y_{t-1}, w = A^T u from the oracle
     u = gi.uniform(p, n, seed, 2)
     w = oracle.matvec(p, np.ascontiguousarray(A.T), u)
     prev = x0
-    rows = gi.words(seed, 3, 64) % np.uint64(n)
     for t in range(iters):
         assert oracle.dot(p, u, Yh[t]) == oracle.dot(p, w, prev), t
-        # sampled rows: y_t[i] = A_i . y_{t-1}
-        for i in rows[:8]:
-            i = int(i)
-            assert int(Yh[t][i]) == oracle.dot(p, A[i], prev), (t, i)
+        # every element: y_t = A y_{t-1}, the oracle's per-term product
+        want = oracle.matvec(p, A, prev)
+        bad = np.nonzero(Yh[t] != want)[0]
+        assert bad.size == 0, (t, bad[:8])
         prev = Yh[t]
 
 
