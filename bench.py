@@ -422,7 +422,8 @@ def run_gpu(args):
             ln = measure_secondary(args, name, g, torch, ctx, stream)
             also[name] = {k: ln[k] for k in ("value", "unit", "ms_per_step", "config", "roofline")
                           if k in ln}
-            for k in ("single_call_us", "graph_of_256_single_dots", "same_gpu", "fields", "p_2^31-1"):
+            for k in ("single_call_us", "graph_of_256_single_dots", "same_gpu", "fields", "p_2^31-1",
+                      "prepared"):
                 if k in ln:
                     also[name][k] = ln[k]
             torch.cuda.empty_cache()
@@ -798,8 +799,21 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                                        ("u64_carry_cuda_core", g.GFP_REPR_U64_CARRY, 3)):
                     ctx.set_repr(rp)
                     large[name] = timed(lambda: g.gfp_matmul_block(ctx, pl, Al, Bl, C, stream), reps)
-                del Al, Bl
             ctx.set_repr(0)
+            # A prepared once (digit images in the layout the tensor cores read),
+            # as for a resident matrix used by many products
+            prep = g.BlockPrep(ctx, p, A)
+            C2 = torch.empty((m, nb), dtype=torch.int32, device="cuda")
+            t_prep = timed(lambda: prep.matmul(ctx, B, C2, stream), max(10, args.steps // 4))
+            prep_bytes, prep_passes = prep.info()
+            prep.close()
+            if not torch.equal(C2, C):
+                raise SystemExit("prepared and unprepared block products differ")
+            if large:
+                prep_l = g.BlockPrep(ctx, pl, Al)
+                large["f16tc_prepared"] = timed(lambda: prep_l.matmul(ctx, Bl, C2, stream),
+                                                max(5, args.steps // 10))
+                prep_l.close()
             assert g.gfp_context_check(ctx) == g.GFP_OK
             t = res["f16tc"]
             # A is read once per residue pass; the residues (4 bytes each) are
@@ -824,8 +838,21 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                 "same_gpu": {n: {"ms": v, "gmacs": macs / (v / 1e3) / 1e9} for n, v in res.items()},
                 "gpu_launches": 2 if passes == 1 else 2 * passes + 1,
             })
+            pbytes = prep_bytes + passes * 4.0 * k * nb + 4.0 * m * nb
+            if passes > 1:
+                pbytes += 2 * passes * 4.0 * m * nb
+            pach = pbytes / (t_prep / 1e3) / 1e9
+            line["prepared"] = {
+                "ms": t_prep, "gmacs": macs / (t_prep / 1e3) / 1e9, "passes": prep_passes,
+                "what": "A prepared once into fp16 digit images (4 bytes per entry per pass), "
+                        "then one product per call (B digits + tensor-core kernel)",
+                "roofline": with_read_peak({"bound": "hbm", "achieved": pach, "peak": peak,
+                                            "unit": "GB/s", "frac": pach / peak,
+                                            "kernel": "k_block_tc (prepared A) + k_block_prep_b",
+                                            "peak_kind": f"{peak_kind} hbm_gbs"})}
             if large:
                 line["p_2^31-1"] = {n: {"ms": v, "gmacs": macs / (v / 1e3) / 1e9} for n, v in large.items()}
+                del Al, Bl
         else:
             row_ptr, col, val = gi.csr_pattern(m, k, 0.01, p, seed)
             rp_d = torch.from_numpy(row_ptr.view(np.int32)).cuda()

@@ -275,6 +275,38 @@ GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64
                                     const uint32_t *A, uint64_t lda, const uint32_t *B,
                                     uint64_t ldb, uint32_t *C, uint64_t ldc, void *stream);
 
+/* A prepared once for repeated block products with the same A (block
+ * Wiedemann-style iterations, a resident matrix serving many requests): the
+ * centred residues of Section 3.2.2 split into the two balanced 8-bit digits
+ * the tensor-core product uses (see gfp_matmul_block), stored as fp16 digit
+ * tiles in the layout its matrix units read, so that each product copies
+ * them as they are, with no per-call conversion.  For p <= 65791 one image of
+ * 4 bytes per entry of A; for larger p one image per residue-pass modulus
+ * (A reduced modulo each), 4 bytes per entry each (gfp_block_prep_info gives
+ * the bytes and the pass count).
+ *   A: device, m x k row-major, lda >= k, canonical residues; not referenced
+ *   after the call returns (it synchronises the device).  m, k >= 1.
+ * GFP_ERR_UNSUPPORTED when no residue passes cover k (p-1)^2; GFP_ERR_NOMEM
+ * when the image does not fit.  The prepared object owns its device memory
+ * until gfp_block_prep_destroy. */
+typedef struct gfp_block_prep gfp_block_prep;
+GFP_API gfp_status gfp_block_prepare(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64_t k,
+                                     const uint32_t *A, uint64_t lda, gfp_block_prep **out);
+/* C = A B mod p for the prepared A (m x k): B device k x nb (ldb >= nb),
+ * C device m x nb (ldc >= nb); the same result as gfp_matmul_block on the
+ * original A.  Two launches (B's digits, the product), or two per residue
+ * pass plus one recombination.  Uses the context's block workspace (grown on
+ * first use of a shape: make that call outside stream capture); calls sharing
+ * one context must not run concurrently on different streams. */
+GFP_API gfp_status gfp_matmul_block_prepared(gfp_ctx *ctx, const gfp_block_prep *prep, uint64_t nb,
+                                             const uint32_t *B, uint64_t ldb, uint32_t *C,
+                                             uint64_t ldc, void *stream);
+/* Device bytes held and residue passes per product (1 for p <= 65791). */
+GFP_API gfp_status gfp_block_prep_info(const gfp_block_prep *prep, uint64_t *bytes,
+                                       uint32_t *passes);
+/* Synchronises the device and frees the prepared images. */
+GFP_API gfp_status gfp_block_prep_destroy(gfp_block_prep *prep);
+
 /* Sparse-row block product: A is m x k in CSR form (row_ptr[m+1] offsets
  * into col[] and val[], column indices < k, values canonical residues), B is
  * k x nb dense.  C[i*ldc + j] = (sum_q val[q] * B[col[q]*ldb + j]) mod p for

@@ -104,6 +104,7 @@ struct Args {
     CUtensorMap tmap_a;       // A as a 2-D uint32 tensor {k, m}, box {BK*KBB, BM}, zero fill
     uint64_t m, k, nb;
     const uint8_t *Bimg;      // [n_tiles][kblocks] tiles of B_TILE_BYTES
+    const uint8_t *Aimg;      // prepared A: [m_tiles][kblocks] digit tiles of A_TILE_BYTES (PREP)
     uint32_t *C;
     uint64_t ldc;
     uint32_t *Cacc;           // m x (n_tiles*NT) u32 partial residue sums (zero outside calls)
@@ -259,7 +260,11 @@ __device__ __forceinline__ void store_digits(const Args &a, const ARegs &r, uint
     }
 }
 
-template <bool PRE>
+// PRE: reduce each input modulo p while splitting it (the residue passes).
+// PREP: A arrives already centred and split, as digit tiles in the exact
+// shared-memory layout (a prepared operand, see k_block_prep_a); the
+// producer bulk-copies whole slots and the converter warps have no work.
+template <bool PRE, bool PREP>
 __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__ Args a)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -308,7 +313,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
             for (int s = 0; s < SLOTS; ++s) armed[s] = -1;
             uint32_t si = 0;   // slot sequence number
             bool ok = true;
-            ptx::prefetch_tensormap(&a.tmap_a);
+            if (!PREP) ptx::prefetch_tensormap(&a.tmap_a);
             for (uint64_t u = u0; u < u1 && ok; ++u) {
                 const UnitPos q = unit_pos(a, u);
                 for (uint32_t kb = q.kb0; kb < q.kb1; kb += KBB, ++si) {
@@ -319,9 +324,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                         break;
                     }
                     const uint32_t fb = ptx::smem_u32(&bars->a_full[s]);
-                    ptx::mbar_arrive_expect_tx(fb, SLOT_BYTES);
-                    ptx::tma_load_2d(ptx::smem_u32(slot_mem + (size_t)s * SLOT_BYTES), &a.tmap_a,
-                                     (int)(kb * BK), (int)(q.mt * BM), fb);
+                    if (PREP) {
+                        // the slot's k-blocks are consecutive tiles of the image
+                        const uint32_t bytes = min((uint32_t)KBB, q.kb1 - kb) * (uint32_t)A_TILE_BYTES;
+                        ptx::mbar_arrive_expect_tx(fb, bytes);
+                        ptx::bulk_g2s(ptx::smem_u32(slot_mem + (size_t)s * SLOT_BYTES),
+                                      a.Aimg + ((uint64_t)q.mt * a.kblocks + kb) * A_TILE_BYTES, bytes, fb);
+                    } else {
+                        ptx::mbar_arrive_expect_tx(fb, SLOT_BYTES);
+                        ptx::tma_load_2d(ptx::smem_u32(slot_mem + (size_t)s * SLOT_BYTES), &a.tmap_a,
+                                         (int)(kb * BK), (int)(q.mt * BM), fb);
+                    }
                     armed[s] = (int)round;
                 }
             }
@@ -387,8 +400,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                     const uint32_t sub = (kb - q.kb0) % KBB;
                     const uint32_t s = si % SLOTS, round = si / SLOTS;
                     const uint32_t sb = it % BSTAGES, roundb = it / BSTAGES;
+                    // the slot's digits: converted in place, or landed ready-made (PREP)
+                    const uint32_t abar = PREP ? ptx::smem_u32(&bars->a_full[s]) : ptx::smem_u32(&bars->conv[s]);
                     if (!wait_bar(ptx::smem_u32(&bars->full_b[sb]), roundb & 1, abort, a.err) ||
-                        (sub == 0 && !wait_bar(ptx::smem_u32(&bars->conv[s]), round & 1, abort, a.err))) {
+                        (sub == 0 && !wait_bar(abar, round & 1, abort, a.err))) {
                         ok = false;
                         break;
                     }
@@ -421,6 +436,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                    ptx::globaltimer() - t0 < WAIT_NS) {
             }
         }
+    } else if (PREP && warp < W_EPI0) {
+        // prepared digits need no conversion: the converter warps stand by
     } else if (warp < W_EPI0) {
         // ---------------- converters: uint32 tiles -> centred fp16 digits, in place ----------------
         const int ct = threadIdx.x - 32 * W_CONV0;   // 0..255
@@ -586,6 +603,39 @@ __global__ void k_block_prep_b(const uint32_t *B, uint64_t ldb, uint64_t k, uint
         const int rh = col, rl = col + 64;
         *reinterpret_cast<uint4 *>(out + rh * 128 + ((j ^ (rh & 7)) << 4)) = wh;
         *reinterpret_cast<uint4 *>(out + rl * 128 + ((j ^ (rl & 7)) << 4)) = wl;
+    }
+}
+
+// A (m x k, row-major uint32 residues, leading dimension lda) -> prepared
+// digit image for one modulus: per (m-tile, k-block) one tile of A_TILE_BYTES
+// holding the high digits and then the low digits, each 128 rows x 64 K fp16
+// in the 128-byte swizzled K-major layout, byte for byte what the converter
+// warps write into a slot.  Entries outside the matrix become digits of 0.
+// With pre != 0 each entry is first reduced modulo mod.p (a residue pass).
+__global__ void __launch_bounds__(256)
+    k_block_prep_a(const uint32_t *__restrict__ A, uint64_t lda, uint64_t m, uint64_t k, Mod mod,
+                   uint32_t half, uint32_t pre_magic, int pre, uint32_t kblocks, uint8_t *img)
+{
+    const uint64_t tile = blockIdx.x;   // mt * kblocks + kb
+    const uint64_t mt = tile / kblocks, kb = tile % kblocks;
+    uint8_t *th = img + tile * A_TILE_BYTES;
+    uint8_t *tl = th + A_DIGIT_BYTES;
+    for (int q = threadIdx.x; q < BM * 16; q += blockDim.x) {
+        const int row = q >> 4, c4 = q & 15;
+        const uint64_t gr = mt * BM + row, gk = kb * BK + (uint64_t)c4 * 4;
+        uint32_t v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            v[e] = (gr < m && gk + e < k) ? __ldg(A + gr * lda + gk + e) : 0u;
+            if (pre) v[e] = reduce_small(v[e], mod.p, pre_magic);
+        }
+        uint32_t h01, l01, h23, l23;
+        split_pair(v[0], v[1], mod.p, half, h01, l01);
+        split_pair(v[2], v[3], mod.p, half, h23, l23);
+        const int j = c4 >> 1, halfsel = c4 & 1;
+        const uint32_t off = (uint32_t)row * 128u + ((uint32_t)(j ^ (row & 7)) << 4) + (halfsel << 3);
+        *reinterpret_cast<uint2 *>(th + off) = make_uint2(h01, h23);
+        *reinterpret_cast<uint2 *>(tl + off) = make_uint2(l01, l23);
     }
 }
 
@@ -799,34 +849,64 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
+size_t block_prep_a_bytes(uint64_t m, uint64_t k)
+{
+    const uint64_t kblocks = (k + blk::BK - 1) / blk::BK;
+    const uint64_t m_tiles = (m + blk::BM - 1) / blk::BM;
+    return (size_t)(m_tiles * kblocks) * blk::A_TILE_BYTES;
+}
+
+cudaError_t launch_block_prep_a(const Mod &mod, uint64_t m, uint64_t k, const uint32_t *A,
+                                uint64_t lda, bool reduce_inputs, uint8_t *img, cudaStream_t s)
+{
+    using namespace blk;
+    const uint64_t kblocks = (k + BK - 1) / BK, m_tiles = (m + BM - 1) / BM;
+    if (m_tiles * kblocks == 0) return cudaSuccess;
+    if (m_tiles * kblocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    k_block_prep_a<<<(unsigned)(m_tiles * kblocks), 256, 0, s>>>(
+        A, lda, m, k, mod, (mod.p - 1) / 2, (uint32_t)((1ull << 32) / mod.p), reduce_inputs ? 1 : 0,
+        (uint32_t)kblocks, img);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb, const uint32_t *A,
                             uint64_t lda, const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc,
-                            void *ws, int sm_count, cudaStream_t s, int *launches, bool reduce_inputs)
+                            void *ws, int sm_count, cudaStream_t s, int *launches, bool reduce_inputs,
+                            const uint8_t *Aimg)
 {
     using namespace blk;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_block_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SMEM_BYTES);
+        cudaError_t e = cudaFuncSetAttribute(k_block_tc<false, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_block_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k_block_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)SMEM_BYTES);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_block_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
-    if (!encode) return cudaErrorNotSupported;
     Args a;
     memset(&a, 0, sizeof a);
-    // A: innermost dimension k (elements), then m rows lda*4 bytes apart
-    const cuuint64_t gdim[2] = {(cuuint64_t)k, (cuuint64_t)m};
-    const cuuint64_t gstride[1] = {(cuuint64_t)lda * 4};
-    const cuuint32_t box[2] = {(cuuint32_t)(BK * KBB), (cuuint32_t)BM};
-    const cuuint32_t estride[2] = {1, 1};
-    if (encode(&a.tmap_a, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, (void *)A, gdim, gstride, box, estride,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
+    if (Aimg) {
+        // prepared digits (16-byte aligned tiles of a device allocation): no tensor map
+        if (((uintptr_t)Aimg) & 15u) return cudaErrorInvalidValue;
+        a.Aimg = Aimg;
+    } else {
+        PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+        if (!encode) return cudaErrorNotSupported;
+        // A: innermost dimension k (elements), then m rows lda*4 bytes apart
+        const cuuint64_t gdim[2] = {(cuuint64_t)k, (cuuint64_t)m};
+        const cuuint64_t gstride[1] = {(cuuint64_t)lda * 4};
+        const cuuint32_t box[2] = {(cuuint32_t)(BK * KBB), (cuuint32_t)BM};
+        const cuuint32_t estride[2] = {1, 1};
+        if (encode(&a.tmap_a, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, (void *)A, gdim, gstride, box, estride,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
     a.m = m;
     a.k = k;
     a.nb = nb;
@@ -856,10 +936,12 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint64_t grid = std::min<uint64_t>(a.units, (uint64_t)sm_count);
-    if (reduce_inputs)
-        k_block_tc<true><<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(a);
+    if (Aimg)   // the image already holds the residues of this pass's modulus
+        k_block_tc<false, true><<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(a);
+    else if (reduce_inputs)
+        k_block_tc<true, false><<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(a);
     else
-        k_block_tc<false><<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(a);
+        k_block_tc<false, false><<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(a);
     *launches += 2;
     return cudaGetLastError();
 }

@@ -125,7 +125,12 @@ size_t block_tc_bimg_bytes(uint64_t k, uint64_t nb);   // the rest must be zero 
 cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb, const uint32_t *A,
                             uint64_t lda, const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc,
                             void *ws, int sm_count, cudaStream_t s, int *launches,
-                            bool reduce_inputs = false);
+                            bool reduce_inputs = false, const uint8_t *Aimg = nullptr);
+// Prepared A: digit image of A for one modulus (block_prep_a_bytes(m, k)
+// bytes), consumed by launch_block_tc through Aimg (A and lda then unused).
+size_t block_prep_a_bytes(uint64_t m, uint64_t k);
+cudaError_t launch_block_prep_a(const Mod &mod, uint64_t m, uint64_t k, const uint32_t *A,
+                                uint64_t lda, bool reduce_inputs, uint8_t *img, cudaStream_t s);
 uint32_t *block_tc_err_flag(void *ws, uint64_t m, uint64_t k, uint64_t nb);
 // Runs the bounded-wait self test; *status_bits gets the device error word.
 cudaError_t wait_selftest(uint64_t limit_ns, cudaStream_t s, uint32_t *status_bits);

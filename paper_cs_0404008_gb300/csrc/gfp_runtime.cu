@@ -765,6 +765,33 @@ static gfp_status check_range_rows(gfp_ctx *ctx, const uint32_t *M, uint64_t row
     return GFP_OK;
 }
 
+// Block-product workspace of the context for shape (m, k, nb) followed by
+// `passes` residue matrices (m x nb uint32 each); the caller holds ctx->mu.
+static gfp_status ensure_block_ws(gfp_ctx *ctx, uint64_t m, uint64_t k, uint64_t nb, int passes,
+                                  cudaStream_t s)
+{
+    const size_t tc_need = block_tc_workspace_bytes(m, k, nb);
+    const size_t need = tc_need + (size_t)passes * m * nb * 4;
+    if (need > ctx->blk_ws_bytes) {
+        GFP_CUDA_TRY(cudaDeviceSynchronize());
+        if (ctx->blk_ws) cudaFree(ctx->blk_ws);
+        ctx->blk_ws = nullptr;
+        ctx->blk_ws_bytes = 0;
+        if (cudaMalloc(&ctx->blk_ws, need) != cudaSuccess) return GFP_ERR_NOMEM;
+        GFP_CUDA_TRY(cudaMemset(ctx->blk_ws, 0, need));
+        ctx->blk_ws_bytes = need;
+    }
+    if (m != ctx->blk_m || k != ctx->blk_k || nb != ctx->blk_nb) {
+        // the partial-sum region moves with the shape: clear it
+        const size_t z = block_tc_bimg_bytes(k, nb);
+        GFP_CUDA_TRY(cudaMemsetAsync((uint8_t *)ctx->blk_ws + z, 0, tc_need - z, s));
+        ctx->blk_m = m;
+        ctx->blk_k = k;
+        ctx->blk_nb = nb;
+    }
+    return GFP_OK;
+}
+
 GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64_t k, uint64_t nb,
                                     const uint32_t *A, uint64_t lda, const uint32_t *B,
                                     uint64_t ldb, uint32_t *C, uint64_t ldc, void *stream)
@@ -817,24 +844,9 @@ GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64
     }
     std::lock_guard<std::mutex> g(ctx->mu);
     const size_t tc_need = block_tc_workspace_bytes(m, k, nb);
-    const size_t rns_bytes = rns_ok ? (size_t)rc.L * m * nb * 4 : 0;   // residue matrices after it
-    const size_t need = tc_need + rns_bytes;
-    if (need > ctx->blk_ws_bytes) {
-        GFP_CUDA_TRY(cudaDeviceSynchronize());
-        if (ctx->blk_ws) cudaFree(ctx->blk_ws);
-        ctx->blk_ws = nullptr;
-        ctx->blk_ws_bytes = 0;
-        if (cudaMalloc(&ctx->blk_ws, need) != cudaSuccess) return GFP_ERR_NOMEM;
-        GFP_CUDA_TRY(cudaMemset(ctx->blk_ws, 0, need));
-        ctx->blk_ws_bytes = need;
-    }
-    if (m != ctx->blk_m || k != ctx->blk_k || nb != ctx->blk_nb) {
-        // the partial-sum region moves with the shape: clear it
-        const size_t z = block_tc_bimg_bytes(k, nb);
-        GFP_CUDA_TRY(cudaMemsetAsync((uint8_t *)ctx->blk_ws + z, 0, tc_need - z, s));
-        ctx->blk_m = m;
-        ctx->blk_k = k;
-        ctx->blk_nb = nb;
+    {
+        const gfp_status st = ensure_block_ws(ctx, m, k, nb, rns_ok ? rc.L : 0, s);
+        if (st != GFP_OK) return st;
     }
     int launches = 0;
     if (!rns_ok) {
@@ -846,6 +858,117 @@ GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64
             GFP_CUDA_TRY(launch_block_tc(make_mod(rc.mod[l]), m, k, nb, A, lda, B, ldb, R + (size_t)l * m * nb,
                                          nb, ctx->blk_ws, ctx->sm_count, s, &launches, true));
         GFP_CUDA_TRY(launch_block_crt(R, m, nb, C, ldc, rc, ctx->sm_count, s));
+        ++launches;
+    }
+    ctx->launches += launches;
+    return GFP_OK;
+}
+
+// A prepared once for repeated block products: its tensor-core digit
+// images, one per modulus (p itself, or each residue-pass modulus).
+struct gfp_block_prep {
+    uint32_t p = 0;
+    uint64_t m = 0, k = 0;
+    int passes = 0;          // 1: p <= 65791 directly; more: residue passes
+    RnsConst rc{};
+    void *mem = nullptr;
+    size_t per = 0;          // bytes of one image
+};
+
+GFP_API gfp_status gfp_block_prepare(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64_t k,
+                                     const uint32_t *A, uint64_t lda, gfp_block_prep **out)
+{
+    GFP_TRACE();
+    if (!out) return GFP_ERR_INVALID;
+    *out = nullptr;
+    if (!ctx || p < 2 || m == 0 || k == 0 || lda < k || !A || (((uintptr_t)A) & 3u))
+        return GFP_ERR_INVALID;
+    RnsConst rc{};
+    int passes = 1;
+    if (p > BLOCK_TC_MAX_P) {
+        if (!block_rns_plan(p, k, &rc)) return GFP_ERR_UNSUPPORTED;
+        passes = rc.L;
+    }
+    if (ctx->validate) {
+        const gfp_status st = check_range_rows(ctx, A, m, k, lda, p, nullptr);
+        if (st != GFP_OK) return st;
+    }
+    gfp_block_prep *pp = new (std::nothrow) gfp_block_prep();
+    if (!pp) return GFP_ERR_NOMEM;
+    pp->per = block_prep_a_bytes(m, k);
+    if (cudaMalloc(&pp->mem, pp->per * passes) != cudaSuccess) {
+        delete pp;
+        return GFP_ERR_NOMEM;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < passes && e == cudaSuccess; ++l)
+        e = launch_block_prep_a(make_mod(passes == 1 ? p : rc.mod[l]), m, k, A, lda, passes > 1,
+                                (uint8_t *)pp->mem + pp->per * l, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        note_cuda_error(e);
+        cudaFree(pp->mem);
+        delete pp;
+        return GFP_ERR_CUDA;
+    }
+    ctx->launches += passes;
+    pp->p = p;
+    pp->m = m;
+    pp->k = k;
+    pp->passes = passes;
+    pp->rc = rc;
+    *out = pp;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_block_prep_info(const gfp_block_prep *pp, uint64_t *bytes, uint32_t *passes)
+{
+    if (!pp) return GFP_ERR_INVALID;
+    if (bytes) *bytes = (uint64_t)pp->per * pp->passes;
+    if (passes) *passes = (uint32_t)pp->passes;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_block_prep_destroy(gfp_block_prep *pp)
+{
+    GFP_TRACE();
+    if (!pp) return GFP_ERR_INVALID;
+    cudaDeviceSynchronize();
+    cudaFree(pp->mem);
+    delete pp;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_matmul_block_prepared(gfp_ctx *ctx, const gfp_block_prep *pp, uint64_t nb,
+                                             const uint32_t *B, uint64_t ldb, uint32_t *C,
+                                             uint64_t ldc, void *stream)
+{
+    GFP_TRACE();
+    if (!ctx || !pp || ldb < nb || ldc < nb) return GFP_ERR_INVALID;
+    if (nb && (!B || !C)) return GFP_ERR_INVALID;
+    if ((((uintptr_t)B) | ((uintptr_t)C)) & 3u) return GFP_ERR_INVALID;
+    if (nb == 0) return GFP_OK;
+    cudaStream_t s = as_stream(stream);
+    const uint64_t m = pp->m, k = pp->k;
+    if (ctx->validate) {
+        const gfp_status st = check_range_rows(ctx, B, k, nb, ldb, pp->p, s);
+        if (st != GFP_OK) return st;
+    }
+    std::lock_guard<std::mutex> g(ctx->mu);
+    const gfp_status st = ensure_block_ws(ctx, m, k, nb, pp->passes > 1 ? pp->passes : 0, s);
+    if (st != GFP_OK) return st;
+    int launches = 0;
+    const uint8_t *img = (const uint8_t *)pp->mem;
+    if (pp->passes == 1) {
+        GFP_CUDA_TRY(launch_block_tc(make_mod(pp->p), m, k, nb, nullptr, 0, B, ldb, C, ldc,
+                                     ctx->blk_ws, ctx->sm_count, s, &launches, false, img));
+    } else {
+        uint32_t *R = (uint32_t *)((uint8_t *)ctx->blk_ws + block_tc_workspace_bytes(m, k, nb));
+        for (int l = 0; l < pp->passes; ++l)
+            GFP_CUDA_TRY(launch_block_tc(make_mod(pp->rc.mod[l]), m, k, nb, nullptr, 0, B, ldb,
+                                         R + (size_t)l * m * nb, nb, ctx->blk_ws, ctx->sm_count, s,
+                                         &launches, true, img + pp->per * l));
+        GFP_CUDA_TRY(launch_block_crt(R, m, nb, C, ldc, pp->rc, ctx->sm_count, s));
         ++launches;
     }
     ctx->launches += launches;

@@ -116,6 +116,10 @@ _SIGS = {
     "gfp_matvec_iterate": (_int, [_vp, _u32, _u64, _vp, _u64, _vp, _vp, _u32, _vp]),
     "gfp_matvec_sequence": (_int, [_vp, _u32, _u64, _vp, _u64, _vp, _vp, _u32, _vp, _vp, _vp]),
     "gfp_matmul_block": (_int, [_vp, _u32, _u64, _u64, _u64, _vp, _u64, _vp, _u64, _vp, _u64, _vp]),
+    "gfp_block_prepare": (_int, [_vp, _u32, _u64, _u64, _vp, _u64, ctypes.POINTER(_vp)]),
+    "gfp_matmul_block_prepared": (_int, [_vp, _vp, _u64, _vp, _u64, _vp, _u64, _vp]),
+    "gfp_block_prep_info": (_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
+    "gfp_block_prep_destroy": (_int, [_vp]),
     "gfp_matmul_block_csr": (_int, [_vp, _u32, _u64, _u64, _u64, _vp, _vp, _vp, _vp, _u64, _vp, _u64,
                                     _vp]),
     "gfp_context_check": (_int, [_vp]),
@@ -467,6 +471,65 @@ def gfp_matmul_block(ctx: Context, p: int, A, B, C, stream=None):
                                    B.stride(0), _ptr(C), C.stride(0), _stream(stream)),
            "gfp_matmul_block")
     return C
+
+
+class BlockPrep:
+    """gfp_block_prep: A prepared once (tensor-core digit images) for repeated
+    block products with the same A."""
+
+    def __init__(self, ctx: Context, p: int, A):
+        m, k = A.shape
+        if A.dtype.itemsize != 4 or A.stride(1) != 1:
+            raise ValueError("A must be a row-major 32-bit matrix")
+        h = _vp()
+        _check(load().gfp_block_prepare(ctx.handle, p, m, k, _ptr(A), A.stride(0), ctypes.byref(h)),
+               "gfp_block_prepare")
+        self.handle, self.p, self.m, self.k = h, p, m, k
+
+    def info(self):
+        b, n = _u64(), _u32()
+        _check(load().gfp_block_prep_info(self.handle, ctypes.byref(b), ctypes.byref(n)),
+               "gfp_block_prep_info")
+        return int(b.value), int(n.value)
+
+    def matmul(self, ctx: Context, B, C, stream=None):
+        k2, nb = B.shape
+        if k2 != self.k or tuple(C.shape) != (self.m, nb):
+            raise ValueError("shape mismatch")
+        for t, name in ((B, "B"), (C, "C")):
+            if t.dtype.itemsize != 4 or t.stride(1) != 1:
+                raise ValueError(f"{name} must be a row-major 32-bit matrix")
+        _check(load().gfp_matmul_block_prepared(ctx.handle, self.handle, nb, _ptr(B), B.stride(0),
+                                                _ptr(C), C.stride(0), _stream(stream)),
+               "gfp_matmul_block_prepared")
+        return C
+
+    def close(self):
+        if self.handle:
+            _check(load().gfp_block_prep_destroy(self.handle), "gfp_block_prep_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gfp_block_prepare(ctx: Context, p: int, A) -> BlockPrep:
+    return BlockPrep(ctx, p, A)
+
+
+def gfp_matmul_block_prepared(ctx: Context, prep: BlockPrep, B, C, stream=None):
+    return prep.matmul(ctx, B, C, stream)
+
+
+def gfp_block_prep_info(prep: BlockPrep):
+    return prep.info()
+
+
+def gfp_block_prep_destroy(prep: BlockPrep):
+    prep.close()
 
 
 def gfp_matmul_block_csr(ctx: Context, p: int, k: int, row_ptr, col, val, B, C, stream=None):

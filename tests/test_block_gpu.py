@@ -36,6 +36,27 @@ def run_block(lib, ctx, p, A, B, lda=None, ldb=None, ldc=None):
     return out[:, :nb]
 
 
+def run_prepared(lib, ctx, p, A, Bs, lda=None, ldc=None):
+    """Prepare A once, then one product per B in Bs; returns the C matrices."""
+    m, k = A.shape
+    prep = lib.BlockPrep(ctx, p, dev2(A, lda))
+    outs = []
+    try:
+        for B in Bs:
+            nb = B.shape[1]
+            Cfull = torch.full((m, ldc or nb), -1, dtype=torch.int32, device="cuda")
+            prep.matmul(ctx, dev2(B), Cfull[:, :nb])
+            torch.cuda.synchronize()
+            assert lib.gfp_context_check(ctx) == lib.GFP_OK
+            out = host(Cfull)
+            if ldc and ldc > nb:
+                assert (out[:, nb:] == 0xFFFFFFFF).all(), "wrote outside C"
+            outs.append(out[:, :nb])
+    finally:
+        prep.close()
+    return outs
+
+
 SHAPES_TC = [(1, 1, 1), (7, 13, 5), (128, 64, 64), (129, 1000, 64), (300, 2049, 70),
              (64, 4101, 3), (257, 1025, 128), (130, 3000, 65)]
 
@@ -174,7 +195,9 @@ def test_block_rns_full_size(lib, fresh):
     A = gi.uniform(p, m * k, seed, 0).reshape(m, k)
     B = gi.uniform(p, k * nb, seed, 1).reshape(k, nb)
     got = run_block(lib, fresh, p, A, B)
-    assert np.array_equal(got, oracle.block(p, A, B))
+    want = oracle.block(p, A, B)
+    assert np.array_equal(got, want)
+    assert np.array_equal(run_prepared(lib, fresh, p, A, [B])[0], want)
 
 
 def test_block_many_units_per_cta(lib, fresh):
@@ -198,6 +221,7 @@ def test_block_full_size_workload(lib, fresh):
     got = run_block(lib, fresh, p, A, B)
     want = oracle.block(p, A, B)
     assert np.array_equal(got, want)
+    assert np.array_equal(run_prepared(lib, fresh, p, A, [B])[0], want)
 
 
 @pytest.mark.parametrize("repr_", [0, 1, 2, 3, 6, 7])
@@ -370,3 +394,54 @@ def test_csr_h16_packed_b(lib, fresh, p):
     store[1:].copy_(torch.from_numpy(B.reshape(-1).view(np.int32)))
     got = _csr_run(lib, fresh, p, k, row_ptr, col, val, B, Bd=store[1:].view(k, nb))
     assert np.array_equal(got, oracle.csr(p, row_ptr, col, val, B))
+
+
+@pytest.mark.parametrize("shape", SHAPES_TC)
+@pytest.mark.parametrize("p", [2, 251, 65521, 65789, 2147483647, 4294967291])
+def test_block_prepared_parity(lib, fresh, p, shape):
+    """A prepared once (digit images, one per residue modulus for p > 65791),
+    then two products with different B: both equal the oracle and the
+    unprepared product.  Ragged row tiles, ragged k-blocks and exact chunks,
+    ragged column tiles; any row stride of A (the preparation reads A with
+    plain loads)."""
+    m, k, nb = shape
+    A = gi.uniform(p, m * k, 62, 0).reshape(m, k)
+    B1 = gi.uniform(p, k * nb, 62, 1).reshape(k, nb)
+    B2 = gi.uniform(p, k * nb, 62, 2).reshape(k, nb)
+    got = run_prepared(lib, fresh, p, A, [B1, B2], lda=k + 1, ldc=nb + 3)
+    assert np.array_equal(got[0], oracle.block(p, A, B1)), (p, shape)
+    assert np.array_equal(got[1], oracle.block(p, A, B2)), (p, shape)
+
+
+@pytest.mark.parametrize("p", [65521, 65789, 4294967291])
+def test_block_prepared_extreme_digits(lib, fresh, p):
+    """Entries at the ends of the centred range ((p-1)/2 and (p+1)/2, the
+    largest digit magnitudes) and all (p-1), over 5000 terms (five exact
+    chunks)."""
+    m, k, nb = 256, 5000, 64
+    h = (p - 1) // 2
+    for a_val, b_val in ((h, h), (h + 1, h + 1), (h, h + 1), (p - 1, p - 1)):
+        A = np.full((m, k), a_val, np.uint32)
+        B = np.full((k, nb), b_val, np.uint32)
+        want = oracle.block(p, A[:1], B)
+        got = run_prepared(lib, fresh, p, A, [B])[0]
+        assert (got == want[0][None, :]).all(), (p, a_val, b_val)
+
+
+def test_block_prepared_info_and_errors(lib, fresh):
+    m, k = 300, 1000
+    A = dev2(gi.uniform(65521, m * k, 63, 0).reshape(m, k))
+    prep = lib.BlockPrep(fresh, 65521, A)
+    kb, mt = (k + 63) // 64, (m + 127) // 128
+    assert prep.info() == (mt * kb * 32768, 1)
+    B = dev2(gi.uniform(65521, (k + 1) * 8, 63, 1).reshape(k + 1, 8))
+    C = torch.zeros((m, 8), dtype=torch.int32, device="cuda")
+    with pytest.raises(ValueError):
+        prep.matmul(fresh, B, C)   # k mismatch is refused before the call
+    prep.close()
+    prep = lib.BlockPrep(fresh, 4294967291, A)
+    assert prep.info()[1] >= 2
+    prep.close()
+    with pytest.raises(lib.GfpError) as ei:
+        lib.BlockPrep(fresh, 1, A)
+    assert ei.value.status == lib.GFP_ERR_INVALID
