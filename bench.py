@@ -928,6 +928,10 @@ def measure_serve(args, g):
     pools = {kind: [(srv.register_matrix(p, side, side, seed=mseed), p, side, mseed)
                     for p, side, mseed in specs]
              for kind, specs in gi.serve_pool_specs(seed).items()}
+    if args.serve_prepared:
+        # block matrices are resident: build their tensor-core digit images once
+        for h, _, _, _ in pools[2]:
+            srv.prepare_matrix(h)
     reqs = gi.serve_requests(args.requests, seed)
 
     def submit(r):
@@ -1082,6 +1086,8 @@ def measure_serve(args, g):
                                "m=k log-uniform [2^10,2^13], nb=64), p uniform over {65521, "
                                "67108859, 4294967291}, server-generated operands",
                    "load": args.load,
+                   "block_matrices": ("prepared at registration (digit images)" if args.serve_prepared
+                                      else "converted on every product"),
                    "checks": "1% of the results recomputed by direct library calls on the same "
                              "operands regenerated on the device; 20 jobs replayed alone"},
         "serve": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -1244,6 +1250,8 @@ def main():
     ap.add_argument("--sweep-table", default=None, help="cpu_sweep: also write a markdown table")
     ap.add_argument("--requests", type=int, default=100000, help="serve: Poisson requests")
     ap.add_argument("--load", type=float, default=0.7, help="serve: arrival rate / capacity")
+    ap.add_argument("--serve-prepared", type=int, default=1,
+                    help="serve: prepare the block matrices' digit images at registration (1) or not (0)")
     ap.add_argument("--block-m", type=int, default=16384, help="block workload rows (profiling)")
     ap.add_argument("--gfq-fields", default=None,
                     help="gfq workload: comma-separated fields p^k (default 2^8,3^10,65521^1)")

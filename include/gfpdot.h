@@ -433,6 +433,14 @@ GFP_API gfp_status gfp_server_destroy(gfp_server *srv);
  * identifies it in MATVEC and BLOCK jobs. */
 GFP_API gfp_status gfp_register_matrix(gfp_server *srv, uint32_t p, uint64_t rows, uint64_t cols,
                                        const uint32_t *dev, uint64_t seed, uint64_t *handle);
+/* Prepare a registered matrix for BLOCK jobs: its tensor-core digit images
+ * (gfp_block_prepare) are built now, held outside the job budget until the
+ * server is destroyed, and every later BLOCK job on it reads them instead of
+ * converting the matrix on each product (results are identical).  Optional;
+ * synchronises the device.  A no-op in simulation mode or when already
+ * prepared.  GFP_ERR_INVALID for an unknown handle, the errors of
+ * gfp_block_prepare otherwise. */
+GFP_API gfp_status gfp_prepare_matrix(gfp_server *srv, uint64_t handle);
 /* Queue a job; never blocks.  GFP_ERR_INVALID for malformed jobs (unknown
  * kind or matrix, p mismatch, zero sizes), GFP_ERR_NOMEM if the job alone
  * exceeds the budget, GFP_ERR_AGAIN if the queue is full. */

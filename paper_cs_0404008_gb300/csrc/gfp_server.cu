@@ -88,6 +88,7 @@ struct Matrix {
     const uint32_t *dev;
     void *owned;
     uint64_t ld;   // leading dimension (server-generated matrices pad rows to 16 bytes)
+    gfp_block_prep *prep = nullptr;   // digit images for block jobs (gfp_prepare_matrix)
 };
 
 enum class State { Queued, Running, Done };
@@ -306,6 +307,8 @@ int32_t gfp_server::launch_one(uint64_t t, Launch &L)
     gfp_status stt;
     if (j.kind == GFP_JOB_MATVEC)
         stt = gfp_matvec(ctx, j.p, M.rows, M.cols, M.dev, M.ld, v, outp, s);
+    else if (M.prep)
+        stt = gfp_matmul_block_prepared(ctx, M.prep, j.nb, v, j.nb, outp, j.nb, s);
     else
         stt = gfp_matmul_block(ctx, j.p, M.rows, M.cols, j.nb, M.dev, M.ld, v, j.nb, outp, j.nb, s);
     st.kernel_launches += gfp_launch_count(ctx) - before;
@@ -554,8 +557,10 @@ GFP_API gfp_status gfp_server_destroy(gfp_server *s)
     if (!s->cfg.simulate) {
         for (auto c : s->ctxs) gfp_context_destroy(c);
         for (auto cs : s->streams) cudaStreamDestroy(cs);
-        for (auto &kv : s->mats)
+        for (auto &kv : s->mats) {
+            if (kv.second.prep) gfp_block_prep_destroy(kv.second.prep);
             if (kv.second.owned) cudaFree(kv.second.owned);
+        }
         if (s->pinned) cudaFreeHost(s->pinned);
         if (s->base) cudaFree(s->base);
     }
@@ -588,6 +593,32 @@ GFP_API gfp_status gfp_register_matrix(gfp_server *s, uint32_t p, uint64_t rows,
     std::lock_guard<std::mutex> g(s->mu);
     *handle = s->next_mat++;
     s->mats[*handle] = M;
+    return GFP_OK;
+}
+
+GFP_API gfp_status gfp_prepare_matrix(gfp_server *s, uint64_t handle)
+{
+    GFP_TRACE();
+    if (!s) return GFP_ERR_INVALID;
+    Matrix M;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        auto it = s->mats.find(handle);
+        if (it == s->mats.end()) return GFP_ERR_INVALID;
+        if (it->second.prep || s->cfg.simulate) return GFP_OK;
+        M = it->second;
+    }
+    if (cudaSetDevice(s->cfg.device) != cudaSuccess) return GFP_ERR_CUDA;
+    gfp_block_prep *pp = nullptr;
+    const gfp_status st = gfp_block_prepare(s->ctxs[0], M.p, M.rows, M.cols, M.dev, M.ld, &pp);
+    if (st != GFP_OK) return st;
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->mats.find(handle);
+    if (it == s->mats.end() || it->second.prep) {
+        gfp_block_prep_destroy(pp);
+        return it == s->mats.end() ? GFP_ERR_INVALID : GFP_OK;
+    }
+    it->second.prep = pp;
     return GFP_OK;
 }
 

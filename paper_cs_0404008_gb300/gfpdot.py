@@ -141,6 +141,7 @@ _SIGS = {
     "gfp_server_destroy": (_int, [_vp]),
     "gfp_register_matrix": (_int, [_vp, _u32, _u64, _u64, _vp, _u64, ctypes.POINTER(_u64)]),
     "gfp_submit": (_int, [_vp, ctypes.POINTER(gfp_job), ctypes.POINTER(_u64)]),
+    "gfp_prepare_matrix": (_int, [_vp, _u64]),
     "gfp_poll": (_int, [_vp, _u64, ctypes.POINTER(gfp_result)]),
     "gfp_wait": (_int, [_vp, _u64, _u64, ctypes.POINTER(gfp_result)]),
     "gfp_result_copy": (_int, [_vp, _u64, _vp, _u64]),
@@ -700,6 +701,10 @@ class Server:
         _check(load().gfp_register_matrix(self.handle, p, rows, cols, _ptr(dev), seed,
                                           ctypes.byref(h)), "gfp_register_matrix")
         return int(h.value)
+
+    def prepare_matrix(self, handle: int):
+        """Build the block-product digit images of a registered matrix now."""
+        _check(load().gfp_prepare_matrix(self.handle, handle), "gfp_prepare_matrix")
 
     def submit_status(self, kind: int, p: int, n: int = 0, nb: int = 0, matrix: int = 0,
                       x=None, y=None, v=None, seed: int = 0):

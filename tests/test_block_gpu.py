@@ -377,7 +377,8 @@ def test_csr_h16_packed_b(lib, fresh, p):
                                             (64, 100, 8, 1.0, 9, 13, True),
                                             (257, 700, 72, 0.0, None, None, False),
                                             (129, 2000, 64, 0.4, None, None, True)):
-        row_ptr, col, val = gi.csr_pattern(m, k, dens, p, seed=76)
+        row_ptr, col, val = gi.csr_pattern(m, k, dens, max(p, 3), seed=76)
+        val = (val % p).astype(np.uint32)   # p = 2: values 0 and 1
         B = gi.uniform(p, k * nb, 76, 3).reshape(k, nb)
         if maxed:
             val = np.full_like(val, p - 1)
@@ -388,7 +389,8 @@ def test_csr_h16_packed_b(lib, fresh, p):
         assert np.array_equal(got, oracle.csr(p, row_ptr, col, val, B)), (p, m, k, nb, ldb, ldc)
     # a B view one element into its storage (the packing reads any layout)
     m, k, nb = 90, 800, 64
-    row_ptr, col, val = gi.csr_pattern(m, k, 0.1, p, seed=77)
+    row_ptr, col, val = gi.csr_pattern(m, k, 0.1, max(p, 3), seed=77)
+    val = (val % p).astype(np.uint32)
     B = gi.uniform(p, k * nb, 77, 1).reshape(k, nb)
     store = torch.zeros(k * nb + 1, dtype=torch.int32, device="cuda")
     store[1:].copy_(torch.from_numpy(B.reshape(-1).view(np.int32)))

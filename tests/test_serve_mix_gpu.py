@@ -5,7 +5,8 @@ The first 2000 requests of the serving workload (the same seeded stream the
 benchmark draws: dot products with n up to 2^22, matrix-vector products on
 registered matrices up to 16384 x 16384, block products up to 8192 x 8192 x 64,
 moduli 65521, 67108859 and 2^32-5) arrive as a Poisson stream at a server
-configured as in the benchmark.  Checked against the oracle: every dot
+configured as in the benchmark, half of the block matrices prepared (digit
+images built at registration) and half not.  Checked against the oracle: every dot
 result, every block result whose modulus exceeds 65791 (the residue-pass
 path of the tensor-core product), every other block result with p = 65521,
 every fourth matrix-vector result and every result on the largest
@@ -36,6 +37,10 @@ def test_served_mix_matches_oracle_and_alone(lib):
         specs = gi.serve_pool_specs(SEED)
         handles = {kind: [srv.register_matrix(p, side, side, seed=ms) for p, side, ms in sp]
                    for kind, sp in specs.items()}
+        # half of the block matrices carry prepared digit images: block jobs on
+        # them take the prepared product, the others convert on every product
+        for i in range(0, 16, 2):
+            srv.prepare_matrix(handles[2][i])
         reqs = gi.serve_requests(COUNT, SEED)
 
         def job_p(r):
