@@ -807,6 +807,8 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
             t_prep = timed(lambda: prep.matmul(ctx, B, C2, stream), max(10, args.steps // 4))
             prep_bytes, prep_passes = prep.info()
             prep.close()
+            g.gfp_matmul_block(ctx, p, A, B, C, stream)   # C was last written by other products
+            torch.cuda.synchronize()
             if not torch.equal(C2, C):
                 raise SystemExit("prepared and unprepared block products differ")
             if large:
@@ -923,7 +925,7 @@ def measure_serve(args, g):
 
     seed = gi.BASE_SEED + 5
     srv = g.Server(device=0, mem_budget=16 << 30, n_streams=8, batch_window_us=50,
-                   max_inflight=256)
+                   max_inflight=256, block_sm_percent=args.serve_block_sms)
     # resident matrix pools (registered once): sides log-uniform
     pools = {kind: [(srv.register_matrix(p, side, side, seed=mseed), p, side, mseed)
                     for p, side, mseed in specs]
@@ -1086,6 +1088,7 @@ def measure_serve(args, g):
                                "m=k log-uniform [2^10,2^13], nb=64), p uniform over {65521, "
                                "67108859, 4294967291}, server-generated operands",
                    "load": args.load,
+                   "block_sm_percent": args.serve_block_sms or 100,
                    "block_matrices": ("prepared at registration (digit images)" if args.serve_prepared
                                       else "converted on every product"),
                    "checks": "1% of the results recomputed by direct library calls on the same "
@@ -1250,6 +1253,8 @@ def main():
     ap.add_argument("--sweep-table", default=None, help="cpu_sweep: also write a markdown table")
     ap.add_argument("--requests", type=int, default=100000, help="serve: Poisson requests")
     ap.add_argument("--load", type=float, default=0.7, help="serve: arrival rate / capacity")
+    ap.add_argument("--serve-block-sms", type=int, default=0,
+                    help="serve: percent of the SMs a block job's kernel may occupy (0: all)")
     ap.add_argument("--serve-prepared", type=int, default=1,
                     help="serve: prepare the block matrices' digit images at registration (1) or not (0)")
     ap.add_argument("--block-m", type=int, default=16384, help="block workload rows (profiling)")

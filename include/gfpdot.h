@@ -378,6 +378,10 @@ typedef struct gfp_server_cfg {
                                    their work (scheduling, admission and API tests without a GPU) */
     uint32_t fail_every;        /* fault injection: every n-th admission attempt fails as if the
                                    device allocation failed (0: off) */
+    uint32_t block_sm_percent;  /* share of the SMs that one BLOCK job's tensor-core kernel may
+                                   occupy, in percent (0 or >= 100: all).  Its persistent CTAs
+                                   fill an SM each; leaving some SMs to the other jobs keeps dot
+                                   and matrix-vector jobs from waiting behind a block job */
 } gfp_server_cfg;
 
 /* A job.  Operands are either caller device pointers (which must stay valid

@@ -234,10 +234,11 @@ __global__ void __launch_bounds__(256, PLAIN ? 4 : 3)
 // first packed into a k x nb uint16 image (k_csr_pack_b16, 2 bytes per
 // element) and each gathered B row carries twice the columns per byte: the
 // L2-to-SM traffic of the gathers, which bounds this product, is halved.
-// Four quarter-warps take alternate groups of four nonzeros; lane l of a
-// quarter owns output columns 8l'..8l'+7 (l' = l mod 8) of the 64-column
-// group and gathers them with one 16-byte load per nonzero, four loads in
-// flight.  Products of residues below 2^16 are below 2^32, and a row holds
+// The four quarter-warps take eight nonzeros each of a chunk of 32; lane l
+// of a quarter owns output columns 8l'..8l'+7 (l' = l mod 8) of the 64-column
+// group and gathers them with one 16-byte load per nonzero, eight loads in
+// flight (the gathers are latency-bound: what matters is how many are
+// outstanding).  Products of residues below 2^16 are below 2^32, and a row holds
 // fewer than 2^32 nonzeros, so plain 64-bit sums never need an interim
 // reduction (the blocked bound of Section 3.1 exceeds 2^32 for p <= 65536);
 // the quarters' residues are added modulo p at the end.
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 3)
     k_block_csr_h16(Mod mod, uint64_t m, uint64_t k, uint64_t nb,
                     const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col,
                     const uint32_t *__restrict__ val, const uint16_t *__restrict__ Bh,
@@ -295,25 +296,29 @@ __global__ void __launch_bounds__(256, 4)
                 }
                 st[lane] = make_uint2(c, v);
                 __syncwarp();
-                const uint32_t steps = (cnt + 15) >> 4;   // 16 nonzeros per warp step
-                for (uint32_t t = 0; t < steps; ++t) {
-                    // pairs 16t + 4 qtr + {0, 1, 2, 3}
-                    const uint4 e01 = st4[8 * t + 2 * qtr];
-                    const uint4 e23 = st4[8 * t + 2 * qtr + 1];
-                    uint4 b[4];
-                    b[0] = __ldg(reinterpret_cast<const uint4 *>(bcol + (uint64_t)e01.x * row_bytes));
-                    b[1] = __ldg(reinterpret_cast<const uint4 *>(bcol + (uint64_t)e01.z * row_bytes));
-                    b[2] = __ldg(reinterpret_cast<const uint4 *>(bcol + (uint64_t)e23.x * row_bytes));
-                    b[3] = __ldg(reinterpret_cast<const uint4 *>(bcol + (uint64_t)e23.z * row_bytes));
-                    const uint32_t vv[4] = {e01.y, e01.w, e23.y, e23.w};
+                // quarter qtr takes pairs 8 qtr .. 8 qtr + 7 of the chunk: eight
+                // gathers in flight per lane, none for pairs past the chunk's end
+                uint4 b[8];
+                uint32_t vv[8];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const uint32_t wds[4] = {b[e].x, b[e].y, b[e].z, b[e].w};
+                for (int e = 0; e < 8; e += 2) {
+                    const uint4 pr = st4[4 * qtr + e / 2];   // pairs 8 qtr + e, + e + 1
+                    vv[e] = pr.y;
+                    vv[e + 1] = pr.w;
+                    const uint32_t i0 = 8 * qtr + e;
+                    b[e] = i0 < cnt ? __ldg(reinterpret_cast<const uint4 *>(bcol + (uint64_t)pr.x * row_bytes))
+                                    : make_uint4(0u, 0u, 0u, 0u);
+                    b[e + 1] = i0 + 1 < cnt
+                                   ? __ldg(reinterpret_cast<const uint4 *>(bcol + (uint64_t)pr.z * row_bytes))
+                                   : make_uint4(0u, 0u, 0u, 0u);
+                }
 #pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            s[2 * h] += (uint64_t)(vv[e] * (wds[h] & 0xFFFFu));
-                            s[2 * h + 1] += (uint64_t)(vv[e] * (wds[h] >> 16));
-                        }
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t wds[4] = {b[e].x, b[e].y, b[e].z, b[e].w};
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        s[2 * h] += (uint64_t)(vv[e] * (wds[h] & 0xFFFFu));
+                        s[2 * h + 1] += (uint64_t)(vv[e] * (wds[h] >> 16));
                     }
                 }
                 __syncwarp();

@@ -43,20 +43,7 @@ __device__ __forceinline__ void accumulate_range(Acc &acc, const Mod &m, const u
 #pragma unroll
             for (int u = 0; u < U; ++u) acc.add4(a[u], c[u], m);
         }
-        if (v < nv) {
-            // fewer than U loads of each operand remain: issue them together
-            uint4 a[U], c[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (v + u * T < nv) {
-                    a[u] = ld_stream4(xv + v + u * T);
-                    c[u] = ld_stream4(yv + v + u * T);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (v + u * T < nv) acc.add4(a[u], c[u], m);
-        }
+        for (; v < nv; v += T) acc.add4(ld_stream4(xv + v), ld_stream4(yv + v), m);
         const uint64_t i = b + (nv << 2) + t;   // fewer than 4 tail elements, T >= 4
         if (i < e) acc.add(ld_stream1(x + i), ld_stream1(y + i), m);
     } else {

@@ -163,6 +163,7 @@ struct gfp_plan_entry {
 struct gfp_ctx {
     int device = 0;
     int sm_count = 0;
+    int blk_sms = 0;   // CTAs of a tensor-core block kernel (0: one per SM); set by the service
     gfp_repr forced = GFP_REPR_AUTO;
     bool validate = false;
     std::atomic<uint64_t> launches{0};

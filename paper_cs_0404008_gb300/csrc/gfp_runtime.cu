@@ -765,6 +765,12 @@ static gfp_status check_range_rows(gfp_ctx *ctx, const uint32_t *M, uint64_t row
     return GFP_OK;
 }
 
+// CTAs of one tensor-core block kernel: one per SM, or the context's cap
+static int block_sms(const gfp_ctx *ctx)
+{
+    return (ctx->blk_sms > 0 && ctx->blk_sms < ctx->sm_count) ? ctx->blk_sms : ctx->sm_count;
+}
+
 // Block-product workspace of the context for shape (m, k, nb) followed by
 // `passes` residue matrices (m x nb uint32 each); the caller holds ctx->mu.
 static gfp_status ensure_block_ws(gfp_ctx *ctx, uint64_t m, uint64_t k, uint64_t nb, int passes,
@@ -850,13 +856,13 @@ GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64
     }
     int launches = 0;
     if (!rns_ok) {
-        GFP_CUDA_TRY(launch_block_tc(mod, m, k, nb, A, lda, B, ldb, C, ldc, ctx->blk_ws, ctx->sm_count,
+        GFP_CUDA_TRY(launch_block_tc(mod, m, k, nb, A, lda, B, ldb, C, ldc, ctx->blk_ws, block_sms(ctx),
                                      s, &launches));
     } else {
         uint32_t *R = (uint32_t *)((uint8_t *)ctx->blk_ws + tc_need);
         for (int l = 0; l < rc.L; ++l)
             GFP_CUDA_TRY(launch_block_tc(make_mod(rc.mod[l]), m, k, nb, A, lda, B, ldb, R + (size_t)l * m * nb,
-                                         nb, ctx->blk_ws, ctx->sm_count, s, &launches, true));
+                                         nb, ctx->blk_ws, block_sms(ctx), s, &launches, true));
         GFP_CUDA_TRY(launch_block_crt(R, m, nb, C, ldc, rc, ctx->sm_count, s));
         ++launches;
     }
@@ -961,12 +967,12 @@ GFP_API gfp_status gfp_matmul_block_prepared(gfp_ctx *ctx, const gfp_block_prep 
     const uint8_t *img = (const uint8_t *)pp->mem;
     if (pp->passes == 1) {
         GFP_CUDA_TRY(launch_block_tc(make_mod(pp->p), m, k, nb, nullptr, 0, B, ldb, C, ldc,
-                                     ctx->blk_ws, ctx->sm_count, s, &launches, false, img));
+                                     ctx->blk_ws, block_sms(ctx), s, &launches, false, img));
     } else {
         uint32_t *R = (uint32_t *)((uint8_t *)ctx->blk_ws + block_tc_workspace_bytes(m, k, nb));
         for (int l = 0; l < pp->passes; ++l)
             GFP_CUDA_TRY(launch_block_tc(make_mod(pp->rc.mod[l]), m, k, nb, nullptr, 0, B, ldb,
-                                         R + (size_t)l * m * nb, nb, ctx->blk_ws, ctx->sm_count, s,
+                                         R + (size_t)l * m * nb, nb, ctx->blk_ws, block_sms(ctx), s,
                                          &launches, true, img + pp->per * l));
         GFP_CUDA_TRY(launch_block_crt(R, m, nb, C, ldc, pp->rc, ctx->sm_count, s));
         ++launches;

@@ -13,6 +13,7 @@
 // A simulation mode runs the same dispatcher without a GPU: a job "completes"
 // after a time proportional to its work, which lets the admission, batching
 // and API logic be tested on a host without CUDA devices.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -505,7 +506,11 @@ GFP_API gfp_status gfp_server_create(const gfp_server_cfg *cfg, gfp_server **out
             s->streams.push_back(cs);
             gfp_ctx *c = nullptr;
             stt = gfp_context_create(s->cfg.device, &c);
-            if (stt == GFP_OK) s->ctxs.push_back(c);
+            if (stt == GFP_OK) {
+                if (s->cfg.block_sm_percent > 0 && s->cfg.block_sm_percent < 100)
+                    c->blk_sms = std::max(1, (int)((uint64_t)c->sm_count * s->cfg.block_sm_percent / 100));
+                s->ctxs.push_back(c);
+            }
         }
         if (stt != GFP_OK) {
             for (auto c : s->ctxs) gfp_context_destroy(c);

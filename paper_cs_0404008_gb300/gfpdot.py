@@ -65,7 +65,7 @@ class gfp_dot_desc(ctypes.Structure):
 class gfp_server_cfg(ctypes.Structure):
     _fields_ = [("device", _int), ("mem_budget", _u64), ("max_inflight", _u32),
                 ("n_streams", _u32), ("queue_capacity", _u32), ("batch_window_us", _u32),
-                ("simulate", _u32), ("fail_every", _u32)]
+                ("simulate", _u32), ("fail_every", _u32), ("block_sm_percent", _u32)]
 
 
 class gfp_job(ctypes.Structure):
@@ -675,12 +675,12 @@ class Server:
 
     def __init__(self, device: int = 0, mem_budget: int = 0, max_inflight: int = 0,
                  n_streams: int = 0, queue_capacity: int = 0, batch_window_us: int = 0,
-                 simulate: bool = False, fail_every: int = 0):
+                 simulate: bool = False, fail_every: int = 0, block_sm_percent: int = 0):
         if not simulate:
             import torch
             torch.cuda.init()
         cfg = gfp_server_cfg(device, mem_budget, max_inflight, n_streams, queue_capacity,
-                             batch_window_us, int(bool(simulate)), fail_every)
+                             batch_window_us, int(bool(simulate)), fail_every, block_sm_percent)
         h = _vp()
         _check(load().gfp_server_create(ctypes.byref(cfg), ctypes.byref(h)), "gfp_server_create")
         self.handle = h
