@@ -371,7 +371,10 @@ typedef struct gfp_server_cfg {
     int device;                 /* CUDA device */
     uint64_t mem_budget;        /* device bytes for job operands and results (0: 4 GiB) */
     uint32_t max_inflight;      /* launches on the GPU at once; a batched dot launch counts once (0: 256) */
-    uint32_t n_streams;         /* stream pool size (0: 4) */
+    uint32_t n_streams;         /* stream pool size (0: 4); with two or more, the first half
+                                   (rounded up) run at the highest stream priority and take
+                                   dot and matrix-vector launches, the rest take block jobs at
+                                   the lowest priority */
     uint32_t queue_capacity;    /* submitted but not admitted jobs before GFP_ERR_AGAIN (0: 65536) */
     uint32_t batch_window_us;   /* dot jobs arriving within this window share one launch (0: none) */
     uint32_t simulate;          /* 1: no GPU; jobs "run" on the host for a time proportional to

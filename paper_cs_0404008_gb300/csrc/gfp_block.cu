@@ -57,21 +57,7 @@ constexpr int BK = 64;             // K per k-block: one 128-byte swizzle row of
 constexpr int NT = 64;             // output columns per n-tile
 constexpr int MMA_N = 2 * NT;      // hi and lo digits of B stacked along N
 constexpr int KC = 16;             // k-blocks per exact chunk (1024 terms)
-#ifndef GFP_BLK_SLOTS
-#define GFP_BLK_SLOTS 3
-#endif
-#ifndef GFP_BLK_BSTAGES
-#define GFP_BLK_BSTAGES 2
-#endif
-#ifndef GFP_BLK_KBB
-#define GFP_BLK_KBB 2
-#endif
-constexpr int KBB = GFP_BLK_KBB;          // k-blocks per A slot (longer row bursts per TMA box)
-constexpr int SLOTS = GFP_BLK_SLOTS;      // A slots: a uint32 box lands (TMA), is converted in
-                                          // place into fp16 digit tiles, then read by the MMAs
-constexpr int BSTAGES = GFP_BLK_BSTAGES;  // B digit tiles in flight (own ring, off the A path)
 constexpr int A_TILE_BYTES = BM * BK * 4;                     // 32 KiB of uint32 per k-block
-constexpr int SLOT_BYTES = KBB * A_TILE_BYTES;
 constexpr int A_DIGIT_BYTES = BM * BK * 2;                    // 16 KiB per digit
 constexpr int B_TILE_BYTES = MMA_N * BK * 2;                  // 16 KiB
 static_assert(A_TILE_BYTES == 2 * A_DIGIT_BYTES, "in-place conversion needs equal sizes");
@@ -83,25 +69,40 @@ constexpr uint32_t TMEM_COLS = 512;   // 2 accumulator sets x 2 digits x 128 col
 constexpr uint64_t WAIT_NS = 2000000000ull;   // bounded waits: 2 s
 constexpr uint32_t IDESC = ptx::idesc_f16_f32(BM, MMA_N);
 
-struct Bars {
-    uint64_t a_full[SLOTS];    // uint32 A tile landed (1 arrival + tx bytes)
-    uint64_t conv[SLOTS];      // digits written in place (one arrival per converter warp)
-    uint64_t a_empty[SLOTS];   // MMAs reading the digits completed (tcgen05.commit)
-    uint64_t full_b[BSTAGES];  // B digit tile landed (1 arrival + tx bytes)
-    uint64_t empty_b[BSTAGES]; // MMAs reading the B tile completed (tcgen05.commit)
-    uint64_t acc_full[2];      // accumulator set ready (tcgen05.commit)
-    uint64_t acc_empty[2];     // accumulator set drained (one arrival per epilogue warp)
-    uint64_t drain;            // all MMAs issued by this CTA completed
-    uint32_t tmem_base;
-    uint32_t abort;
-    uint32_t last_flag;
+// Pipeline depths: SLOTS shared-memory slots of KBB k-blocks of A each, and
+// BSTAGES B digit tiles.  A slot receives a uint32 box (TMA) that the
+// converter warps turn into fp16 digit tiles in place, or, for a prepared A,
+// ready digit tiles (bulk copy).  The uint32 path measured fastest with three
+// two-k-block slots (longer TMA row bursts) and two B stages; prepared digits
+// only stream through, and four one-k-block slots with four B stages suit
+// them (16384 x 16384 x 64: 0.192 ms against 0.226 ms).
+template <int SLOTS_, int BSTAGES_, int KBB_>
+struct Pipe {
+    static constexpr int SLOTS = SLOTS_, BSTAGES = BSTAGES_, KBB = KBB_;
+    static constexpr int SLOT_BYTES = KBB * A_TILE_BYTES;
+    struct Bars {
+        uint64_t a_full[SLOTS];    // A tile landed (1 arrival + tx bytes)
+        uint64_t conv[SLOTS];      // digits written in place (one arrival per converter warp)
+        uint64_t a_empty[SLOTS];   // MMAs reading the digits completed (tcgen05.commit)
+        uint64_t full_b[BSTAGES];  // B digit tile landed (1 arrival + tx bytes)
+        uint64_t empty_b[BSTAGES]; // MMAs reading the B tile completed (tcgen05.commit)
+        uint64_t acc_full[2];      // accumulator set ready (tcgen05.commit)
+        uint64_t acc_empty[2];     // accumulator set drained (one arrival per epilogue warp)
+        uint64_t drain;            // all MMAs issued by this CTA completed
+        uint32_t tmem_base;
+        uint32_t abort;
+        uint32_t last_flag;
+    };
+    static constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + (size_t)SLOTS * SLOT_BYTES +
+                                         (size_t)BSTAGES * B_TILE_BYTES + 1024;
+    static_assert(sizeof(Bars) <= 1024, "barriers fit their reserve");
+    static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 };
-constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + (size_t)SLOTS * SLOT_BYTES +
-                              (size_t)BSTAGES * B_TILE_BYTES + 1024;
-static_assert(SMEM_BYTES <= 232448, "shared memory per block");
+using PipeU32 = Pipe<3, 2, 2>;    // uint32 A, converted in place
+using PipePrep = Pipe<4, 4, 1>;   // prepared A digits
 
 struct Args {
-    CUtensorMap tmap_a;       // A as a 2-D uint32 tensor {k, m}, box {BK*KBB, BM}, zero fill
+    CUtensorMap tmap_a;       // A as a 2-D uint32 tensor {k, m}, box {BK*KBB, BM} (uint32 pipe), zero fill
     uint64_t m, k, nb;
     const uint8_t *Bimg;      // [n_tiles][kblocks] tiles of B_TILE_BYTES
     const uint8_t *Aimg;      // prepared A: [m_tiles][kblocks] digit tiles of A_TILE_BYTES (PREP)
@@ -215,6 +216,7 @@ struct ARegs {
 };
 
 // sub-tile `sub` of a slot holding KBB k-blocks (row stride BK*4*KBB bytes)
+template <int KBB>
 __device__ __forceinline__ void load_tile(const uint8_t *slot, int sub, int ct, ARegs &r)
 {
 #pragma unroll
@@ -264,9 +266,12 @@ __device__ __forceinline__ void store_digits(const Args &a, const ARegs &r, uint
 // PREP: A arrives already centred and split, as digit tiles in the exact
 // shared-memory layout (a prepared operand, see k_block_prep_a); the
 // producer bulk-copies whole slots and the converter warps have no work.
-template <bool PRE, bool PREP>
+template <bool PRE, bool PREP, class P>
 __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__ Args a)
 {
+    constexpr int SLOTS = P::SLOTS, BSTAGES = P::BSTAGES, KBB = P::KBB;
+    constexpr int SLOT_BYTES = P::SLOT_BYTES;
+    using Bars = typename P::Bars;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *slot_mem = smem;                                  // SLOTS A slots
@@ -458,7 +463,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                 ARegs r[KBB];
 #pragma unroll
                 for (int sub = 0; sub < KBB; ++sub)
-                    if ((uint32_t)sub < nsub) load_tile(slot, sub, ct, r[sub]);
+                    if ((uint32_t)sub < nsub) load_tile<KBB>(slot, sub, ct, r[sub]);
                 asm volatile("bar.sync 2, %0;" ::"n"(CONV_WARPS * 32) : "memory");
 #pragma unroll
                 for (int sub = 0; sub < KBB; ++sub)
@@ -877,14 +882,15 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
     using namespace blk;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_block_tc<false, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cudaError_t e = cudaFuncSetAttribute(k_block_tc<false, false, PipeU32>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)PipeU32::SMEM_BYTES);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_block_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)SMEM_BYTES);
+            e = cudaFuncSetAttribute(k_block_tc<true, false, PipeU32>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipeU32::SMEM_BYTES);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_block_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)SMEM_BYTES);
+            e = cudaFuncSetAttribute(k_block_tc<false, true, PipePrep>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipePrep::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -900,7 +906,7 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
         // A: innermost dimension k (elements), then m rows lda*4 bytes apart
         const cuuint64_t gdim[2] = {(cuuint64_t)k, (cuuint64_t)m};
         const cuuint64_t gstride[1] = {(cuuint64_t)lda * 4};
-        const cuuint32_t box[2] = {(cuuint32_t)(BK * KBB), (cuuint32_t)BM};
+        const cuuint32_t box[2] = {(cuuint32_t)(BK * PipeU32::KBB), (cuuint32_t)BM};
         const cuuint32_t estride[2] = {1, 1};
         if (encode(&a.tmap_a, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, (void *)A, gdim, gstride, box, estride,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -937,11 +943,11 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
     if (e != cudaSuccess) return e;
     const uint64_t grid = std::min<uint64_t>(a.units, (uint64_t)sm_count);
     if (Aimg)   // the image already holds the residues of this pass's modulus
-        k_block_tc<false, true><<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(a);
+        k_block_tc<false, true, PipePrep><<<(unsigned)grid, THREADS, PipePrep::SMEM_BYTES, s>>>(a);
     else if (reduce_inputs)
-        k_block_tc<true, false><<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(a);
+        k_block_tc<true, false, PipeU32><<<(unsigned)grid, THREADS, PipeU32::SMEM_BYTES, s>>>(a);
     else
-        k_block_tc<false, false><<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(a);
+        k_block_tc<false, false, PipeU32><<<(unsigned)grid, THREADS, PipeU32::SMEM_BYTES, s>>>(a);
     *launches += 2;
     return cudaGetLastError();
 }

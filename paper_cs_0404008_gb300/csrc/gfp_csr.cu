@@ -234,11 +234,11 @@ __global__ void __launch_bounds__(256, PLAIN ? 4 : 3)
 // first packed into a k x nb uint16 image (k_csr_pack_b16, 2 bytes per
 // element) and each gathered B row carries twice the columns per byte: the
 // L2-to-SM traffic of the gathers, which bounds this product, is halved.
-// The four quarter-warps take eight nonzeros each of a chunk of 32; lane l
-// of a quarter owns output columns 8l'..8l'+7 (l' = l mod 8) of the 64-column
-// group and gathers them with one 16-byte load per nonzero, eight loads in
-// flight (the gathers are latency-bound: what matters is how many are
-// outstanding).  Products of residues below 2^16 are below 2^32, and a row holds
+// Lane l of quarter-warp qtr owns output columns 8l'..8l'+7 (l' = l mod 8)
+// of the 64-column group and gathers them with one 16-byte load per nonzero;
+// the quarters take alternate groups of four nonzeros.  The gathers are
+// bound by latency, not bytes: what matters is how many are outstanding and
+// how many memory round trips each row waits for in sequence.  Products of residues below 2^16 are below 2^32, and a row holds
 // fewer than 2^32 nonzeros, so plain 64-bit sums never need an interim
 // reduction (the blocked bound of Section 3.1 exceeds 2^32 for p <= 65536);
 // the quarters' residues are added modulo p at the end.
@@ -253,13 +253,53 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-__global__ void __launch_bounds__(256, 3)
+// Gathers of one step: quarter qtr takes pairs 16 t + 4 qtr + {0, 1, 2, 3}
+// of the staged round (pairs past cnt issue no load).
+__device__ __forceinline__ void h16_issue(const uint4 *st4, uint32_t t, int qtr, uint32_t cnt,
+                                          const char *bcol, uint64_t row_bytes, uint4 (&b)[4],
+                                          uint32_t (&v)[4])
+{
+    const uint4 e01 = st4[8 * t + 2 * qtr];
+    const uint4 e23 = st4[8 * t + 2 * qtr + 1];
+    const uint32_t i0 = 16 * t + 4 * qtr;
+    const uint32_t c[4] = {e01.x, e01.z, e23.x, e23.z};
+    v[0] = e01.y;
+    v[1] = e01.w;
+    v[2] = e23.y;
+    v[3] = e23.w;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        b[e] = (i0 + e < cnt) ? __ldg(reinterpret_cast<const uint4 *>(bcol + (uint64_t)c[e] * row_bytes))
+                              : make_uint4(0u, 0u, 0u, 0u);
+}
+
+__device__ __forceinline__ void h16_consume(const uint4 (&b)[4], const uint32_t (&v)[4],
+                                            uint64_t (&s)[8])
+{
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const uint32_t w[4] = {b[e].x, b[e].y, b[e].z, b[e].w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            s[2 * h] += (uint64_t)(v[e] * (w[h] & 0xFFFFu));
+            s[2 * h + 1] += (uint64_t)(v[e] * (w[h] >> 16));
+        }
+    }
+}
+
+// One warp per row.  The row's (column, value) pairs are read in rounds of up
+// to 256 with all loads of a round issued at once (one memory round trip per
+// round, not per 32 pairs) and staged in shared memory; the gathers of step
+// t + 1 are issued before the products of step t are added, so every lane has
+// two steps of gathers outstanding; the next row's bounds are loaded while
+// the current row is processed.
+__global__ void __launch_bounds__(256, 2)
     k_block_csr_h16(Mod mod, uint64_t m, uint64_t k, uint64_t nb,
                     const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col,
                     const uint32_t *__restrict__ val, const uint16_t *__restrict__ Bh,
                     uint32_t *__restrict__ C, uint64_t ldc)
 {
-    __shared__ __align__(16) uint2 stage[8][32];
+    __shared__ __align__(16) uint2 stage[8][256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int qtr = lane >> 3, ql = lane & 7;
     uint2 *st = stage[w];
@@ -267,8 +307,18 @@ __global__ void __launch_bounds__(256, 3)
     const uint64_t warps = (uint64_t)gridDim.x * 8;
     const uint64_t row_bytes = nb * 2;   // a multiple of 16 (nb % 8 == 0)
     const bool cvec = ((((uintptr_t)C) & 15u) == 0) && (ldc % 4 == 0);
-    for (uint64_t row = (uint64_t)blockIdx.x * 8 + w; row < m; row += warps) {
-        const uint32_t q0 = __ldg(row_ptr + row), q1 = __ldg(row_ptr + row + 1);
+    uint64_t row = (uint64_t)blockIdx.x * 8 + w;
+    uint32_t q0 = 0, q1 = 0;
+    if (row < m) {
+        q0 = __ldg(row_ptr + row);
+        q1 = __ldg(row_ptr + row + 1);
+    }
+    for (; row < m; row += warps) {
+        uint32_t n0 = 0, n1 = 0;
+        if (row + warps < m) {
+            n0 = __ldg(row_ptr + row + warps);
+            n1 = __ldg(row_ptr + row + warps + 1);
+        }
         for (uint64_t c0 = 0; c0 < nb; c0 += 64) {
             const uint64_t ca = c0 + 8 * (uint64_t)ql;
             const bool va = ca < nb;   // nb % 8 == 0: all eight columns are valid
@@ -276,52 +326,40 @@ __global__ void __launch_bounds__(256, 3)
             uint64_t s[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) s[j] = 0;
-            uint32_t cn = 0, vn = 0;
-            if (q0 < q1 && (uint32_t)lane < q1 - q0) {
-                cn = __ldg(col + q0 + lane);
-                vn = __ldg(val + q0 + lane);
-            }
-            for (uint32_t q = q0; q < q1; q += 32) {
-                const uint32_t cnt = min(32u, q1 - q);
-                uint32_t c = cn, v = vn;
-                cn = 0;
-                vn = 0;
-                if (q1 - q > 32 && (uint32_t)lane < q1 - q - 32) {
-                    cn = __ldg(col + q + 32 + lane);
-                    vn = __ldg(val + q + 32 + lane);
+            for (uint32_t qb = q0; qb < q1; qb += 256) {
+                const uint32_t cnt = min(256u, q1 - qb);
+                uint32_t pc[8], pv[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t i = 32 * j + lane;
+                    pc[j] = i < cnt ? __ldg(col + qb + i) : 0u;
+                    pv[j] = i < cnt ? __ldg(val + qb + i) : 0u;
                 }
-                if (c >= k) {   // outside the matrix (and lanes past the end): value 0 at column 0
-                    c = 0;
-                    v = 0;
+                __syncwarp();   // the previous round's pairs are no longer read
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const bool in = pc[j] < k;   // outside the matrix: value 0 at column 0
+                    st[32 * j + lane] = make_uint2(in ? pc[j] : 0u, in ? pv[j] : 0u);
                 }
-                st[lane] = make_uint2(c, v);
                 __syncwarp();
-                // quarter qtr takes pairs 8 qtr .. 8 qtr + 7 of the chunk: eight
-                // gathers in flight per lane, none for pairs past the chunk's end
-                uint4 b[8];
-                uint32_t vv[8];
+                const uint32_t steps = (cnt + 15) >> 4;
+                uint4 b[4];
+                uint32_t v[4];
+                h16_issue(st4, 0, qtr, cnt, bcol, row_bytes, b, v);
+                for (uint32_t t = 0; t < steps; ++t) {
+                    uint4 bn[4];
+                    uint32_t vn[4];
+                    const bool more = t + 1 < steps;
+                    if (more) h16_issue(st4, t + 1, qtr, cnt, bcol, row_bytes, bn, vn);
+                    h16_consume(b, v, s);
+                    if (more) {
 #pragma unroll
-                for (int e = 0; e < 8; e += 2) {
-                    const uint4 pr = st4[4 * qtr + e / 2];   // pairs 8 qtr + e, + e + 1
-                    vv[e] = pr.y;
-                    vv[e + 1] = pr.w;
-                    const uint32_t i0 = 8 * qtr + e;
-                    b[e] = i0 < cnt ? __ldg(reinterpret_cast<const uint4 *>(bcol + (uint64_t)pr.x * row_bytes))
-                                    : make_uint4(0u, 0u, 0u, 0u);
-                    b[e + 1] = i0 + 1 < cnt
-                                   ? __ldg(reinterpret_cast<const uint4 *>(bcol + (uint64_t)pr.z * row_bytes))
-                                   : make_uint4(0u, 0u, 0u, 0u);
-                }
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const uint32_t wds[4] = {b[e].x, b[e].y, b[e].z, b[e].w};
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        s[2 * h] += (uint64_t)(vv[e] * (wds[h] & 0xFFFFu));
-                        s[2 * h + 1] += (uint64_t)(vv[e] * (wds[h] >> 16));
+                        for (int e = 0; e < 4; ++e) {
+                            b[e] = bn[e];
+                            v[e] = vn[e];
+                        }
                     }
                 }
-                __syncwarp();
             }
             uint32_t r[8];
 #pragma unroll
@@ -343,6 +381,8 @@ __global__ void __launch_bounds__(256, 3)
                 }
             }
         }
+        q0 = n0;
+        q1 = n1;
     }
 }
 

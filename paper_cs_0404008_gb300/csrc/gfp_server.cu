@@ -6,8 +6,10 @@
 //              output bytes fit in the device arena (memory-based admission)
 //   launch  -> all dot jobs admitted in one dispatcher pass share ONE
 //              persistent batched kernel launch; matrix-vector and block jobs
-//              launch individually; launches rotate over a pool of streams,
-//              so work of different jobs overlaps on the device
+//              launch individually; launches rotate over a pool of streams
+//              (dot and matrix-vector on high-priority streams, block jobs on
+//              low-priority ones), so work of different jobs overlaps on the
+//              device and short jobs' CTAs are scheduled first
 //   complete-> the dispatcher polls a completion event per launch, frees the
 //              operands, publishes the result and wakes waiters
 // A simulation mode runs the same dispatcher without a GPU: a job "completes"
@@ -142,7 +144,8 @@ struct gfp_server {
     std::vector<gfp_ctx *> ctxs;
     uint32_t *pinned = nullptr;
     std::vector<int> pinned_free;
-    int rr = 0;
+    int rr = 0, rr_blk = 0;   // next stream of each class
+    int n_fast = 0;           // streams [0, n_fast) carry dot and matrix-vector launches
     gfp_server_stats st{};
 
     uint64_t footprint(const gfp_job &j, uint64_t *op, uint64_t *out) const;
@@ -391,9 +394,17 @@ bool gfp_server::admit_and_launch()
     }
     if (dots.empty() && others.empty()) return false;
 
-    auto start = [&](Launch &L) {
-        L.stream = rr;
-        rr = (rr + 1) % (int)streams.size();
+    // dot and matrix-vector launches rotate over the high-priority streams,
+    // block launches over the low-priority ones (all of them when there is one)
+    auto start = [&](Launch &L, bool block) {
+        const int nf = n_fast, ns = (int)streams.size();
+        if (block && ns > nf) {
+            L.stream = nf + rr_blk;
+            rr_blk = (rr_blk + 1) % (ns - nf);
+        } else {
+            L.stream = rr;
+            rr = (rr + 1) % nf;
+        }
         if (!cfg.simulate && cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming) != cudaSuccess)
             L.status = GFP_ERR_CUDA;
     };
@@ -401,7 +412,7 @@ bool gfp_server::admit_and_launch()
     if (!dots.empty()) {
         Launch L;
         L.tickets = dots;
-        start(L);
+        start(L, false);
         double sim = 0;
         for (uint64_t tk : dots) {
             JobRec &r = jobs.at(tk);
@@ -435,7 +446,7 @@ bool gfp_server::admit_and_launch()
     for (uint64_t tk : others) {
         Launch L;
         L.tickets = {tk};
-        start(L);
+        start(L, jobs.at(tk).job.kind == GFP_JOB_BLOCK);
         JobRec &r = jobs.at(tk);
         r.res.t_start_ns = t_start;
         r.res.batch = 1;
@@ -497,9 +508,16 @@ GFP_API gfp_status gfp_server_create(const gfp_server_cfg *cfg, gfp_server **out
             s->pinned = nullptr;
             stt = GFP_ERR_NOMEM;
         }
+        // with two or more streams, the first half get the highest priority
+        // (dot and matrix-vector jobs) and the rest the lowest (block jobs):
+        // CTAs of short jobs are scheduled ahead of a block kernel's
+        int lo_prio = 0, hi_prio = 0;
+        if (cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess) lo_prio = hi_prio = 0;
+        s->n_fast = s->cfg.n_streams >= 2 ? (int)(s->cfg.n_streams + 1) / 2 : 1;
         for (uint32_t i = 0; stt == GFP_OK && i < s->cfg.n_streams; ++i) {
             cudaStream_t cs;
-            if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+            const int prio = (int)i < s->n_fast ? hi_prio : lo_prio;
+            if (cudaStreamCreateWithPriority(&cs, cudaStreamNonBlocking, prio) != cudaSuccess) {
                 stt = GFP_ERR_CUDA;
                 break;
             }
@@ -522,6 +540,7 @@ GFP_API gfp_status gfp_server_create(const gfp_server_cfg *cfg, gfp_server **out
         }
     } else {
         s->streams.resize(s->cfg.n_streams, nullptr);
+        s->n_fast = s->cfg.n_streams >= 2 ? (int)(s->cfg.n_streams + 1) / 2 : 1;
     }
     for (int i = (int)kPinnedBlocks - 1; i >= 0; --i) s->pinned_free.push_back(i);
     s->disp = std::thread([s] { s->dispatcher(); });
