@@ -880,7 +880,7 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
             cmacs = float(nnz) * nb
             abytes = 8.0 * nnz + 4.0 * (m + 1) + 4.0 * k * nb + 4.0 * m * nb
             # gathers from L2: one B row (nb stored elements) per nonzero
-            csr_kernel, bpe = ("k_block_csr_h16", 2) if p <= 65536 else ("k_block_csr_wide", 4)
+            csr_kernel, bpe = "k_block_csr_wide", 4
             gbytes = float(nnz) * nb * bpe
             l2p = own_peaks()["read_l2"]
             line.update({
@@ -1253,7 +1253,7 @@ def main():
     ap.add_argument("--sweep-table", default=None, help="cpu_sweep: also write a markdown table")
     ap.add_argument("--requests", type=int, default=100000, help="serve: Poisson requests")
     ap.add_argument("--load", type=float, default=0.7, help="serve: arrival rate / capacity")
-    ap.add_argument("--serve-block-sms", type=int, default=0,
+    ap.add_argument("--serve-block-sms", type=int, default=50,
                     help="serve: percent of the SMs a block job's kernel may occupy (0: all)")
     ap.add_argument("--serve-prepared", type=int, default=1,
                     help="serve: prepare the block matrices' digit images at registration (1) or not (0)")

@@ -312,14 +312,9 @@ GFP_API gfp_status gfp_block_prep_destroy(gfp_block_prep *prep);
  * k x nb dense.  C[i*ldc + j] = (sum_q val[q] * B[col[q]*ldb + j]) mod p for
  * row_ptr[i] <= q < row_ptr[i+1].  All arrays on the device; row_ptr must be
  * non-decreasing with row_ptr[0] = 0 (checked on the device only when
- * validation is enabled, together with col < k and the residues).  One launch,
- * or two when p <= 65536, nb is a multiple of 8 and the blocked representation
- * applies: B is then first packed to 16 bits per residue in a context
- * workspace (k * nb * 2 bytes, grown by the first call that needs more, so
- * make that call outside stream capture), which halves the bytes of the B-row
- * gathers.  k == 0 writes zeros.  Representation: the one forced on the
- * context, else the built-in rule for p (tuned plans do not apply).  Calls
- * sharing one context must not run concurrently on different streams. */
+ * validation is enabled, together with col < k and the residues).  One launch;
+ * k == 0 writes zeros.  Representation: the one forced on the context, else
+ * the built-in rule for p (tuned plans do not apply). */
 GFP_API gfp_status gfp_matmul_block_csr(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64_t k,
                                         uint64_t nb, const uint32_t *row_ptr, const uint32_t *col,
                                         const uint32_t *val, const uint32_t *B, uint64_t ldb,

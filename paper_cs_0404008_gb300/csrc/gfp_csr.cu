@@ -230,191 +230,6 @@ __global__ void __launch_bounds__(256, PLAIN ? 4 : 3)
     }
 }
 
-// Narrow form, for p <= 65536: every residue of B fits 16 bits, so B is
-// first packed into a k x nb uint16 image (k_csr_pack_b16, 2 bytes per
-// element) and each gathered B row carries twice the columns per byte: the
-// L2-to-SM traffic of the gathers, which bounds this product, is halved.
-// Lane l of quarter-warp qtr owns output columns 8l'..8l'+7 (l' = l mod 8)
-// of the 64-column group and gathers them with one 16-byte load per nonzero;
-// the quarters take alternate groups of four nonzeros.  The gathers are
-// bound by latency, not bytes: what matters is how many are outstanding and
-// how many memory round trips each row waits for in sequence.  Products of residues below 2^16 are below 2^32, and a row holds
-// fewer than 2^32 nonzeros, so plain 64-bit sums never need an interim
-// reduction (the blocked bound of Section 3.1 exceeds 2^32 for p <= 65536);
-// the quarters' residues are added modulo p at the end.
-__global__ void __launch_bounds__(256)
-    k_csr_pack_b16(uint64_t k, uint64_t nb, const uint32_t *__restrict__ B, uint64_t ldb,
-                   uint16_t *__restrict__ Bh)
-{
-    const uint64_t n = k * nb, T = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += T) {
-        const uint64_t r = i / nb, c = i - r * nb;
-        Bh[i] = (uint16_t)__ldg(B + r * ldb + c);
-    }
-}
-
-// Gathers of one step: quarter qtr takes pairs 16 t + 4 qtr + {0, 1, 2, 3}
-// of the staged round (pairs past cnt issue no load).
-__device__ __forceinline__ void h16_issue(const uint4 *st4, uint32_t t, int qtr, uint32_t cnt,
-                                          const char *bcol, uint64_t row_bytes, uint4 (&b)[4],
-                                          uint32_t (&v)[4])
-{
-    const uint4 e01 = st4[8 * t + 2 * qtr];
-    const uint4 e23 = st4[8 * t + 2 * qtr + 1];
-    const uint32_t i0 = 16 * t + 4 * qtr;
-    const uint32_t c[4] = {e01.x, e01.z, e23.x, e23.z};
-    v[0] = e01.y;
-    v[1] = e01.w;
-    v[2] = e23.y;
-    v[3] = e23.w;
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-        b[e] = (i0 + e < cnt) ? __ldg(reinterpret_cast<const uint4 *>(bcol + (uint64_t)c[e] * row_bytes))
-                              : make_uint4(0u, 0u, 0u, 0u);
-}
-
-__device__ __forceinline__ void h16_consume(const uint4 (&b)[4], const uint32_t (&v)[4],
-                                            uint64_t (&s)[8])
-{
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const uint32_t w[4] = {b[e].x, b[e].y, b[e].z, b[e].w};
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            s[2 * h] += (uint64_t)(v[e] * (w[h] & 0xFFFFu));
-            s[2 * h + 1] += (uint64_t)(v[e] * (w[h] >> 16));
-        }
-    }
-}
-
-// One warp per row.  The row's (column, value) pairs are read in rounds of up
-// to 256 with all loads of a round issued at once (one memory round trip per
-// round, not per 32 pairs) and staged in shared memory; the gathers of step
-// t + 1 are issued before the products of step t are added, so every lane has
-// two steps of gathers outstanding; the next row's bounds are loaded while
-// the current row is processed.
-__global__ void __launch_bounds__(256, 2)
-    k_block_csr_h16(Mod mod, uint64_t m, uint64_t k, uint64_t nb,
-                    const uint32_t *__restrict__ row_ptr, const uint32_t *__restrict__ col,
-                    const uint32_t *__restrict__ val, const uint16_t *__restrict__ Bh,
-                    uint32_t *__restrict__ C, uint64_t ldc)
-{
-    __shared__ __align__(16) uint2 stage[8][256];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int qtr = lane >> 3, ql = lane & 7;
-    uint2 *st = stage[w];
-    const uint4 *st4 = reinterpret_cast<const uint4 *>(st);
-    const uint64_t warps = (uint64_t)gridDim.x * 8;
-    const uint64_t row_bytes = nb * 2;   // a multiple of 16 (nb % 8 == 0)
-    const bool cvec = ((((uintptr_t)C) & 15u) == 0) && (ldc % 4 == 0);
-    uint64_t row = (uint64_t)blockIdx.x * 8 + w;
-    uint32_t q0 = 0, q1 = 0;
-    if (row < m) {
-        q0 = __ldg(row_ptr + row);
-        q1 = __ldg(row_ptr + row + 1);
-    }
-    for (; row < m; row += warps) {
-        uint32_t n0 = 0, n1 = 0;
-        if (row + warps < m) {
-            n0 = __ldg(row_ptr + row + warps);
-            n1 = __ldg(row_ptr + row + warps + 1);
-        }
-        for (uint64_t c0 = 0; c0 < nb; c0 += 64) {
-            const uint64_t ca = c0 + 8 * (uint64_t)ql;
-            const bool va = ca < nb;   // nb % 8 == 0: all eight columns are valid
-            const char *bcol = reinterpret_cast<const char *>(Bh + (va ? ca : 0));
-            uint64_t s[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) s[j] = 0;
-            for (uint32_t qb = q0; qb < q1; qb += 256) {
-                const uint32_t cnt = min(256u, q1 - qb);
-                uint32_t pc[8], pv[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const uint32_t i = 32 * j + lane;
-                    pc[j] = i < cnt ? __ldg(col + qb + i) : 0u;
-                    pv[j] = i < cnt ? __ldg(val + qb + i) : 0u;
-                }
-                __syncwarp();   // the previous round's pairs are no longer read
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const bool in = pc[j] < k;   // outside the matrix: value 0 at column 0
-                    st[32 * j + lane] = make_uint2(in ? pc[j] : 0u, in ? pv[j] : 0u);
-                }
-                __syncwarp();
-                const uint32_t steps = (cnt + 15) >> 4;
-                uint4 b[4];
-                uint32_t v[4];
-                h16_issue(st4, 0, qtr, cnt, bcol, row_bytes, b, v);
-                for (uint32_t t = 0; t < steps; ++t) {
-                    uint4 bn[4];
-                    uint32_t vn[4];
-                    const bool more = t + 1 < steps;
-                    if (more) h16_issue(st4, t + 1, qtr, cnt, bcol, row_bytes, bn, vn);
-                    h16_consume(b, v, s);
-                    if (more) {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            b[e] = bn[e];
-                            v[e] = vn[e];
-                        }
-                    }
-                }
-            }
-            uint32_t r[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                uint32_t x = reduce64(s[j], mod);
-                uint32_t y = __shfl_xor_sync(0xffffffffu, x, 8);
-                x = (x + y >= mod.p) ? x + y - mod.p : x + y;   // x, y < p <= 2^16
-                y = __shfl_xor_sync(0xffffffffu, x, 16);
-                r[j] = (x + y >= mod.p) ? x + y - mod.p : x + y;
-            }
-            if (qtr == 0 && va) {
-                uint32_t *out = C + row * ldc + ca;
-                if (cvec) {
-                    *reinterpret_cast<uint4 *>(out) = make_uint4(r[0], r[1], r[2], r[3]);
-                    *reinterpret_cast<uint4 *>(out + 4) = make_uint4(r[4], r[5], r[6], r[7]);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) out[j] = r[j];
-                }
-            }
-        }
-        q0 = n0;
-        q1 = n1;
-    }
-}
-
-bool csr_h16_eligible(Repr r, uint32_t p, uint64_t k, uint64_t nb)
-{
-    return r == U64_BLOCK && p <= 65536u && nb % 8 == 0 && k <= (1ull << 40) && nb <= (1ull << 20);
-}
-
-cudaError_t launch_block_csr_h16(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
-                                 const uint32_t *row_ptr, const uint32_t *col, const uint32_t *val,
-                                 const uint32_t *B, uint64_t ldb, uint16_t *Bh, uint32_t *C,
-                                 uint64_t ldc, int sm_count, cudaStream_t s)
-{
-    uint64_t pb = (k * nb + 255) / 256;
-    if (pb > (uint64_t)sm_count * 8) pb = (uint64_t)sm_count * 8;
-    k_csr_pack_b16<<<(unsigned)pb, 256, 0, s>>>(k, nb, B, ldb, Bh);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    static int occ = 0;
-    if (!occ) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_block_csr_h16, 256, 0) != cudaSuccess ||
-            occ < 1)
-            occ = 1;
-    }
-    uint64_t blocks = (m + 7) / 8;
-    const uint64_t cap = (uint64_t)sm_count * occ;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    k_block_csr_h16<<<(unsigned)blocks, 256, 0, s>>>(mod, m, k, nb, row_ptr, col, val, Bh, C, ldc);
-    return cudaGetLastError();
-}
-
 template <class Acc, bool PLAIN>
 static int csr_wide_blocks_per_sm()
 {

@@ -143,12 +143,6 @@ cudaError_t launch_block_csr(Repr r, const Mod &mod, uint64_t kbound, uint64_t m
                              const uint32_t *row_ptr, const uint32_t *col, const uint32_t *val,
                              const uint32_t *B, uint64_t ldb, uint32_t *C, uint64_t ldc,
                              int sm_count, cudaStream_t s);
-// The 16-bit gather form for p <= 65536 (B packed into Bh, k * nb uint16).
-bool csr_h16_eligible(Repr r, uint32_t p, uint64_t k, uint64_t nb);
-cudaError_t launch_block_csr_h16(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
-                                 const uint32_t *row_ptr, const uint32_t *col, const uint32_t *val,
-                                 const uint32_t *B, uint64_t ldb, uint16_t *Bh, uint32_t *C,
-                                 uint64_t ldc, int sm_count, cudaStream_t s);
 
 }  // namespace gfp
 
@@ -195,9 +189,6 @@ struct gfp_ctx {
     // flag); zero outside calls except the B image; grown on demand
     void *blk_ws = nullptr;
     size_t blk_ws_bytes = 0;
-    // sparse-row product: B packed to 16 bits (p <= 65536); grown on demand
-    uint16_t *csr_b16 = nullptr;
-    size_t csr_b16_bytes = 0;
     uint64_t blk_m = 0, blk_k = 0, blk_nb = 0;   // shape whose error flag is live
 
     // tuned plan: (p, lg_n) -> entry

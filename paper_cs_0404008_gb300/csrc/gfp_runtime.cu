@@ -457,7 +457,6 @@ GFP_API gfp_status gfp_context_destroy(gfp_ctx *ctx)
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->stage_out) cudaFree(ctx->stage_out);
     if (ctx->blk_ws) cudaFree(ctx->blk_ws);
-    if (ctx->csr_b16) cudaFree(ctx->csr_b16);
     delete ctx;
     return GFP_OK;
 }
@@ -1014,22 +1013,6 @@ GFP_API gfp_status gfp_matmul_block_csr(gfp_ctx *ctx, uint32_t p, uint64_t m, ui
     }
     if (k == 0) {   // no column can hold a nonzero: C = 0 (B has no rows to read)
         GFP_CUDA_TRY(cudaMemset2DAsync(C, ldc * 4, 0, nb * 4, m, s));
-        return GFP_OK;
-    }
-    if (csr_h16_eligible(r, p, k, nb)) {
-        const size_t need = (size_t)k * nb * 2;
-        if (ctx->csr_b16_bytes < need) {
-            if (ctx->csr_b16) cudaFree(ctx->csr_b16);
-            ctx->csr_b16 = nullptr;
-            ctx->csr_b16_bytes = 0;
-            void *mem = nullptr;
-            if (cudaMalloc(&mem, need) != cudaSuccess) return GFP_ERR_NOMEM;
-            ctx->csr_b16 = (uint16_t *)mem;
-            ctx->csr_b16_bytes = need;
-        }
-        GFP_CUDA_TRY(launch_block_csr_h16(make_mod(p), m, k, nb, row_ptr, col, val, B, ldb,
-                                          ctx->csr_b16, C, ldc, ctx->sm_count, s));
-        ctx->launches += 2;
         return GFP_OK;
     }
     GFP_CUDA_TRY(launch_block_csr(r, make_mod(p), k_for(r, p), m, k, nb, row_ptr, col, val, B, ldb,

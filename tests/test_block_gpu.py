@@ -363,41 +363,6 @@ def test_bounded_wait_expires_and_context_survives(lib, fresh):
     assert np.array_equal(run_block(lib, fresh, p, A, B), oracle.block(p, A, B))
 
 
-@pytest.mark.parametrize("p", [2, 3, 251, 65521, 65536])
-def test_csr_h16_packed_b(lib, fresh, p):
-    """The 16-bit gather form (p <= 65536, nb a multiple of 8, blocked
-    representation): B packed to 16 bits per residue before the gathers.
-    Several 64-column groups with a ragged last group of 8, rows of many
-    32-nonzero chunks with ragged tails, empty rows, padded and unaligned
-    leading dimensions, a B view not 16-byte aligned, and all-(p-1) operands
-    (the largest products).  Two launches per call show the packed form ran."""
-    fresh.set_repr(0)
-    for m, k, nb, dens, ldb, ldc, maxed in ((300, 5000, 128, 0.05, None, None, False),
-                                            (40, 3000, 136, 0.3, 141, 137, False),
-                                            (64, 100, 8, 1.0, 9, 13, True),
-                                            (257, 700, 72, 0.0, None, None, False),
-                                            (129, 2000, 64, 0.4, None, None, True)):
-        row_ptr, col, val = gi.csr_pattern(m, k, dens, max(p, 3), seed=76)
-        val = (val % p).astype(np.uint32)   # p = 2: values 0 and 1
-        B = gi.uniform(p, k * nb, 76, 3).reshape(k, nb)
-        if maxed:
-            val = np.full_like(val, p - 1)
-            B = np.full_like(B, p - 1)
-        before = fresh.launch_count()
-        got = _csr_run(lib, fresh, p, k, row_ptr, col, val, B, ldb, ldc)
-        assert fresh.launch_count() - before == 2
-        assert np.array_equal(got, oracle.csr(p, row_ptr, col, val, B)), (p, m, k, nb, ldb, ldc)
-    # a B view one element into its storage (the packing reads any layout)
-    m, k, nb = 90, 800, 64
-    row_ptr, col, val = gi.csr_pattern(m, k, 0.1, max(p, 3), seed=77)
-    val = (val % p).astype(np.uint32)
-    B = gi.uniform(p, k * nb, 77, 1).reshape(k, nb)
-    store = torch.zeros(k * nb + 1, dtype=torch.int32, device="cuda")
-    store[1:].copy_(torch.from_numpy(B.reshape(-1).view(np.int32)))
-    got = _csr_run(lib, fresh, p, k, row_ptr, col, val, B, Bd=store[1:].view(k, nb))
-    assert np.array_equal(got, oracle.csr(p, row_ptr, col, val, B))
-
-
 @pytest.mark.parametrize("shape", SHAPES_TC)
 @pytest.mark.parametrize("p", [2, 251, 65521, 65789, 2147483647, 4294967291])
 def test_block_prepared_parity(lib, fresh, p, shape):
