@@ -92,24 +92,20 @@ struct Pipe {
         uint32_t tmem_base;
         uint32_t abort;
         uint32_t last_flag;
-        uint32_t kb_done;          // k-blocks converted (LDG: paces the L2 prefetches)
     };
     static constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + (size_t)SLOTS * SLOT_BYTES +
                                          (size_t)BSTAGES * B_TILE_BYTES + 1024;
     static_assert(sizeof(Bars) <= 1024, "barriers fit their reserve");
     static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 };
-using PipeU32 = Pipe<3, 2, 2>;    // uint32 A by TMA, converted in place
+using PipeU32 = Pipe<3, 2, 2>;    // uint32 A, converted in place
 using PipePrep = Pipe<4, 4, 1>;   // prepared A digits
-using PipeLdg = Pipe<4, 4, 1>;    // uint32 A loaded into registers, digits written to the slot
 
 struct Args {
     CUtensorMap tmap_a;       // A as a 2-D uint32 tensor {k, m}, box {BK*KBB, BM} (uint32 pipe), zero fill
     uint64_t m, k, nb;
     const uint8_t *Bimg;      // [n_tiles][kblocks] tiles of B_TILE_BYTES
     const uint8_t *Aimg;      // prepared A: [m_tiles][kblocks] digit tiles of A_TILE_BYTES (PREP)
-    const uint32_t *A;        // uint32 A and its row stride (LDG)
-    uint64_t lda;
     uint32_t *C;
     uint64_t ldc;
     uint32_t *Cacc;           // m x (n_tiles*NT) u32 partial residue sums (zero outside calls)
@@ -266,39 +262,11 @@ __device__ __forceinline__ void store_digits(const Args &a, const ARegs &r, uint
     }
 }
 
-// LDG: converter thread ct's eight 16-byte chunks of the (mt, kb) tile of the
-// uint32 A, read from global memory (from L2, where the producer warp has
-// prefetched the tile): chunk i is row (ct + 256 i) / 16, K columns
-// 4 ((ct + 256 i) mod 16) .. + 3 of the k-block.  Rows past m and columns
-// past k read as 0 (rows are 16-byte aligned and lda >= k rounded up to a
-// multiple of 4, so a chunk that starts below k stays inside its row).
-__device__ __forceinline__ void ldg_tile(const Args &a, uint32_t mt, uint32_t kb, int ct, ARegs &r)
-{
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int q = ct + 256 * i;
-        const uint64_t gr = (uint64_t)mt * BM + (q >> 4);
-        const uint64_t gk = (uint64_t)kb * BK + (uint64_t)(q & 15) * 4;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (gr < a.m && gk < a.k) {
-            v = __ldcg(reinterpret_cast<const uint4 *>(a.A + gr * a.lda + gk));
-            if (gk + 1 >= a.k) v.y = 0u;
-            if (gk + 2 >= a.k) v.z = 0u;
-            if (gk + 3 >= a.k) v.w = 0u;
-        }
-        r.v[i] = v;
-    }
-}
-
 // PRE: reduce each input modulo p while splitting it (the residue passes).
 // PREP: A arrives already centred and split, as digit tiles in the exact
 // shared-memory layout (a prepared operand, see k_block_prep_a); the
 // producer bulk-copies whole slots and the converter warps have no work.
-// LDG: the converter warps read A straight into registers (the next tile's
-// loads in flight while the current one is split) and write the digits into
-// a free slot; the producer warp only prefetches tiles into L2, a few slots
-// ahead.  A's uint32 words then never pass through shared memory.
-template <bool PRE, bool PREP, bool LDG, class P>
+template <bool PRE, bool PREP, class P>
 __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__ Args a)
 {
     constexpr int SLOTS = P::SLOTS, BSTAGES = P::BSTAGES, KBB = P::KBB;
@@ -331,7 +299,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
         ptx::mbar_init(ptx::smem_u32(&bars->drain), 1);
         bars->abort = 0;
         bars->last_flag = 0;
-        bars->kb_done = 0;
         ptx::fence_barrier_init();
     }
     if (warp == W_MMA) {
@@ -344,32 +311,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
     const uint32_t tmem = bars->tmem_base;
     volatile uint32_t *abort = &bars->abort;
 
-    if (LDG && warp == W_APROD) {
-        // ---------------- L2 prefetch of the uint32 A tiles, 2 SLOTS k-blocks ahead ----------------
-        if (lane == 0) {
-            volatile uint32_t *done = &bars->kb_done;
-            ptx::prefetch_tensormap(&a.tmap_a);
-            uint32_t si = 0;
-            bool ok = true;
-            for (uint64_t u = u0; u < u1 && ok; ++u) {
-                const UnitPos q = unit_pos(a, u);
-                for (uint32_t kb = q.kb0; kb < q.kb1; ++kb, ++si) {
-                    // pace: at most 2 SLOTS tiles beyond what the converters finished
-                    // (bounded: give up with the abort flag or after the wait limit)
-                    uint64_t t0 = 0;
-                    while (si >= *done + 2u * SLOTS) {
-                        if (*abort) { ok = false; break; }
-                        const uint64_t t = ptx::globaltimer();
-                        if (t0 == 0) t0 = t;
-                        else if (t - t0 > WAIT_NS) { ok = false; break; }
-                        ptx::nanosleep(200);
-                    }
-                    if (!ok) break;
-                    ptx::tma_prefetch_l2_2d(&a.tmap_a, (int)(kb * BK), (int)(q.mt * BM));
-                }
-            }
-        }
-    } else if (warp == W_APROD) {
+    if (warp == W_APROD) {
         // ---------------- producer: uint32 A tiles (TMA) into free slots ----------------
         if (lane == 0) {
             int armed[SLOTS];
@@ -501,49 +443,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
         }
     } else if (PREP && warp < W_EPI0) {
         // prepared digits need no conversion: the converter warps stand by
-    } else if (LDG && warp < W_EPI0) {
-        // ---------------- converters: uint32 A from global into registers -> digits in a slot ----------------
-        const int ct = threadIdx.x - 32 * W_CONV0;   // 0..255
-        if (u0 < u1) {
-            uint64_t u = u0;
-            UnitPos q = unit_pos(a, u);
-            uint32_t kb = q.kb0, si = 0;
-            ARegs cur, nxt;
-            ldg_tile(a, q.mt, kb, ct, cur);
-            for (;;) {
-                // the next tile of this CTA's sequence goes in flight first
-                uint64_t un = u;
-                UnitPos qn = q;
-                uint32_t kbn = kb + 1;
-                bool more = true;
-                if (kbn >= q.kb1) {
-                    un = u + 1;
-                    if (un < u1) {
-                        qn = unit_pos(a, un);
-                        kbn = qn.kb0;
-                    } else {
-                        more = false;
-                    }
-                }
-                if (more) ldg_tile(a, qn.mt, kbn, ct, nxt);
-                const uint32_t s = si % SLOTS, round = si / SLOTS;
-                // the slot's previous digits must have been read by the MMAs
-                const bool got =
-                    round == 0 || warp_wait(ptx::smem_u32(&bars->a_empty[s]), (round - 1) & 1, abort, a.err);
-                if (ptx::bar_red_or<2, CONV_WARPS * 32>(!got || *abort != 0)) break;
-                store_digits<PRE>(a, cur, slot_mem + (size_t)s * SLOT_BYTES, ct);
-                ptx::fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&bars->conv[s]));
-                if (warp == W_CONV0 && lane == 0) *(volatile uint32_t *)&bars->kb_done = si + 1;
-                ++si;
-                if (!more) break;
-                u = un;
-                q = qn;
-                kb = kbn;
-                cur = nxt;
-            }
-        }
     } else if (warp < W_EPI0) {
         // ---------------- converters: uint32 tiles -> centred fp16 digits, in place ----------------
         const int ct = threadIdx.x - 32 * W_CONV0;   // 0..255
@@ -955,10 +854,6 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// uint32 A: converter warps load it into registers (true) or TMA lands it in
-// the slots for in-place conversion (false)
-constexpr bool kALdg = true;
-
 size_t block_prep_a_bytes(uint64_t m, uint64_t k)
 {
     const uint64_t kblocks = (k + blk::BK - 1) / blk::BK;
@@ -987,20 +882,14 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
     using namespace blk;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_block_tc<false, false, false, PipeU32>,
+        cudaError_t e = cudaFuncSetAttribute(k_block_tc<false, false, PipeU32>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)PipeU32::SMEM_BYTES);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_block_tc<true, false, false, PipeU32>,
+            e = cudaFuncSetAttribute(k_block_tc<true, false, PipeU32>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipeU32::SMEM_BYTES);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_block_tc<false, false, true, PipeLdg>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipeLdg::SMEM_BYTES);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_block_tc<true, false, true, PipeLdg>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipeLdg::SMEM_BYTES);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_block_tc<false, true, false, PipePrep>,
+            e = cudaFuncSetAttribute(k_block_tc<false, true, PipePrep>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipePrep::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr = true;
@@ -1017,7 +906,7 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
         // A: innermost dimension k (elements), then m rows lda*4 bytes apart
         const cuuint64_t gdim[2] = {(cuuint64_t)k, (cuuint64_t)m};
         const cuuint64_t gstride[1] = {(cuuint64_t)lda * 4};
-        const cuuint32_t box[2] = {(cuuint32_t)(BK * (kALdg ? PipeLdg::KBB : PipeU32::KBB)), (cuuint32_t)BM};
+        const cuuint32_t box[2] = {(cuuint32_t)(BK * PipeU32::KBB), (cuuint32_t)BM};
         const cuuint32_t estride[2] = {1, 1};
         if (encode(&a.tmap_a, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, (void *)A, gdim, gstride, box, estride,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1053,18 +942,12 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint64_t grid = std::min<uint64_t>(a.units, (uint64_t)sm_count);
-    a.A = A;
-    a.lda = lda;
     if (Aimg)   // the image already holds the residues of this pass's modulus
-        k_block_tc<false, true, false, PipePrep><<<(unsigned)grid, THREADS, PipePrep::SMEM_BYTES, s>>>(a);
-    else if (kALdg && reduce_inputs)
-        k_block_tc<true, false, true, PipeLdg><<<(unsigned)grid, THREADS, PipeLdg::SMEM_BYTES, s>>>(a);
-    else if (kALdg)
-        k_block_tc<false, false, true, PipeLdg><<<(unsigned)grid, THREADS, PipeLdg::SMEM_BYTES, s>>>(a);
+        k_block_tc<false, true, PipePrep><<<(unsigned)grid, THREADS, PipePrep::SMEM_BYTES, s>>>(a);
     else if (reduce_inputs)
-        k_block_tc<true, false, false, PipeU32><<<(unsigned)grid, THREADS, PipeU32::SMEM_BYTES, s>>>(a);
+        k_block_tc<true, false, PipeU32><<<(unsigned)grid, THREADS, PipeU32::SMEM_BYTES, s>>>(a);
     else
-        k_block_tc<false, false, false, PipeU32><<<(unsigned)grid, THREADS, PipeU32::SMEM_BYTES, s>>>(a);
+        k_block_tc<false, false, PipeU32><<<(unsigned)grid, THREADS, PipeU32::SMEM_BYTES, s>>>(a);
     *launches += 2;
     return cudaGetLastError();
 }

@@ -97,17 +97,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int 
         : "memory");
 }
 
-// 2-D tile at (x, y) brought into L2 only (no shared-memory destination, no
-// completion to wait for); the same alignment rule for x
-__device__ __forceinline__ void tma_prefetch_l2_2d(const void *tmap, int x, int y)
-{
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(tmap), "r"(x),
-                 "r"(y)
-                 : "memory");
-}
-
-__device__ __forceinline__ void nanosleep(uint32_t ns) { asm volatile("nanosleep.u32 %0;" ::"r"(ns)); }
-
 // ---- tcgen05 ----
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols)
 {
