@@ -364,7 +364,8 @@ typedef enum gfp_job_kind { GFP_JOB_DOT = 0, GFP_JOB_MATVEC = 1, GFP_JOB_BLOCK =
 
 typedef struct gfp_server_cfg {
     int device;                 /* CUDA device */
-    uint64_t mem_budget;        /* device bytes for job operands and results (0: 4 GiB) */
+    uint64_t mem_budget;        /* device bytes for job operands and results (0: the
+                                   environment variable GFP_MEM_BUDGET, in bytes, else 4 GiB) */
     uint32_t max_inflight;      /* launches on the GPU at once; a batched dot launch counts once (0: 256) */
     uint32_t n_streams;         /* stream pool size (0: 4); with two or more, the first half
                                    (rounded up) run at the highest stream priority and take

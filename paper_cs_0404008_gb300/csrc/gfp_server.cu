@@ -17,6 +17,7 @@
 // and API logic be tested on a host without CUDA devices.
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -490,7 +491,11 @@ GFP_API gfp_status gfp_server_create(const gfp_server_cfg *cfg, gfp_server **out
     gfp_server *s = new (std::nothrow) gfp_server();
     if (!s) return GFP_ERR_NOMEM;
     s->cfg = *cfg;
-    if (!s->cfg.mem_budget) s->cfg.mem_budget = 4ull << 30;
+    if (!s->cfg.mem_budget) {
+        const char *e = getenv("GFP_MEM_BUDGET");   // bytes; the default is 4 GiB
+        const unsigned long long b = e ? strtoull(e, nullptr, 10) : 0ull;
+        s->cfg.mem_budget = b ? (uint64_t)b : 4ull << 30;
+    }
     if (!s->cfg.max_inflight) s->cfg.max_inflight = 256;
     if (!s->cfg.n_streams) s->cfg.n_streams = 4;
     if (!s->cfg.queue_capacity) s->cfg.queue_capacity = 65536;

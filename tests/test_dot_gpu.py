@@ -265,3 +265,45 @@ def test_matvec_sequence_projection(lib, fresh, p, n, iters):
             assert host(seq)[:iters + 1].tolist() == want, use_y
         if use_y:
             assert int(host(Y)[(iters - 1) * n]) == int(xt[0])
+
+
+@pytest.mark.parametrize("p", [65521, 2147483647])
+def test_wiedemann_checkpoint_resume(lib, fresh, p):
+    """Checkpoint and resume of the iteration: 64 steps in one call equal 32
+    steps, the state (t = 32, x_32) saved to the host and the device copies
+    dropped, then 32 more steps started from the restored x_32.  The scalar
+    sequence u^T A^t x resumes the same way: the second half's sequence is
+    the tail of the whole one.  Both are checked against the oracle chain."""
+    n, iters, half = 1536, 64, 32
+    A = gi.uniform(p, n * n, 53, 0).reshape(n, n)
+    x0 = gi.uniform(p, n, 53, 1)
+    u = gi.uniform(p, n, 53, 2)
+    Ad, ud = dev2(A), dev(u)
+    Y = empty(n * iters)
+    lib.gfp_matvec_iterate(fresh, p, Ad, dev(x0), Y, iters)
+    seq = empty(iters + 1)
+    lib.gfp_matvec_sequence(fresh, p, Ad, dev(x0), ud, seq, iters)
+    torch.cuda.synchronize()
+    whole, whole_seq = host(Y)[:n * iters].reshape(iters, n), host(seq)[:iters + 1]
+    # first half, then a checkpoint on the host
+    Y1 = empty(n * half)
+    lib.gfp_matvec_iterate(fresh, p, Ad, dev(x0), Y1, half)
+    torch.cuda.synchronize()
+    ckpt = {"t": half, "x": host(Y1)[(half - 1) * n:half * n].copy()}
+    del Y1
+    torch.cuda.empty_cache()
+    # resume from the checkpoint
+    Y2 = empty(n * half)
+    lib.gfp_matvec_iterate(fresh, p, Ad, dev(ckpt["x"]), Y2, iters - ckpt["t"])
+    seq2 = empty(iters - half + 1)
+    lib.gfp_matvec_sequence(fresh, p, Ad, dev(ckpt["x"]), ud, seq2, iters - half)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(Y2)[:n * half].reshape(half, n), whole[half:])
+    assert np.array_equal(host(seq2)[:iters - half + 1], whole_seq[half:])
+    # the oracle chain, every element of every step
+    xt = x0
+    for t in range(iters):
+        assert int(oracle.dot(p, u, xt)) == int(whole_seq[t]), t
+        xt = oracle.matvec(p, A, xt)
+        assert np.array_equal(whole[t], xt), t
+    assert int(oracle.dot(p, u, xt)) == int(whole_seq[iters])

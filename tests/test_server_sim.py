@@ -131,3 +131,16 @@ def test_destroy_cancels_pending(lib):
     t0 = time.time()
     s.close()
     assert time.time() - t0 < 5
+
+
+def test_memory_budget_from_environment(lib, monkeypatch):
+    """mem_budget 0 takes GFP_MEM_BUDGET (bytes) when set."""
+    monkeypatch.setenv("GFP_MEM_BUDGET", str(3 << 20))
+    s = lib.Server(simulate=True)
+    try:
+        assert s.stats()["mem_budget"] == 3 << 20
+        # a job larger than the budget alone is refused
+        st, _ = s.submit_status(lib.GFP_JOB_DOT, 65521, n=1 << 20, seed=1)
+        assert st == lib.GFP_ERR_NOMEM
+    finally:
+        s.close()
