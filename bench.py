@@ -851,6 +851,8 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                 "roofline": with_read_peak({"bound": "hbm", "achieved": pach, "peak": peak,
                                             "unit": "GB/s", "frac": pach / peak,
                                             "kernel": "k_block_tc (prepared A) + k_block_prep_b",
+                                            "traffic": (traffic_for("k_block_tc_prepared", pbytes)
+                                                        if passes == 1 else None),
                                             "peak_kind": f"{peak_kind} hbm_gbs"})}
             if large:
                 line["p_2^31-1"] = {n: {"ms": v, "gmacs": macs / (v / 1e3) / 1e9} for n, v in large.items()}
