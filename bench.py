@@ -213,12 +213,30 @@ def traffic_record(kernel: str):
         return None
     if not rec:
         return None
-    h = hashlib.sha256()
-    for f in rec.get("sources", []):
-        h.update(open(os.path.join(ROOT, f), "rb").read())
-    if h.hexdigest() != rec.get("sha256"):
+    if source_hash(rec.get("sources", [])) != rec.get("sha256"):
         return None
     return rec
+
+
+def source_hash(files) -> str:
+    """SHA-256 of the sources a traffic record was captured from, as the
+    release build compiles them: blocks under `#ifdef GFP_DEVICE_CHECKS`,
+    `GFP_DCHECK(` lines and blank lines are left out."""
+    h = hashlib.sha256()
+    for f in files:
+        skip = False
+        for line in open(os.path.join(ROOT, f), encoding="utf-8"):
+            st = line.strip()
+            if st.startswith("#ifdef GFP_DEVICE_CHECKS"):
+                skip = True
+                continue
+            if skip:
+                skip = not st.startswith("#endif")
+                continue
+            if not st or "GFP_DCHECK(" in line:
+                continue
+            h.update(line.encode())
+    return h.hexdigest()
 
 
 def traffic_for(kernel: str, alg_bytes: float):

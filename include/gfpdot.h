@@ -323,7 +323,12 @@ GFP_API gfp_status gfp_matmul_block_csr(gfp_ctx *ctx, uint32_t p, uint64_t m, ui
 /* Synchronise the context's device and report whether a kernel of the
  * context gave up on a bounded wait since the last check (GFP_ERR_TIMEOUT,
  * after which the workspace is cleared so later calls start clean), or a
- * CUDA error is pending (GFP_ERR_CUDA).  GFP_OK otherwise. */
+ * CUDA error is pending (GFP_ERR_CUDA).  In a library built with device-side
+ * checks (GFP_DEVICE_CHECKS), also GFP_ERR_INVALID when a kernel met input
+ * outside its contract since the last check (a sparse-row column >= k or a
+ * decreasing row_ptr, a batched work unit outside its pair); the kernels
+ * skip such input instead of faulting, and the check clears the record.
+ * GFP_OK otherwise. */
 GFP_API gfp_status gfp_context_check(gfp_ctx *ctx);
 
 /* Failure-detection self test (no counterpart in the paper): launches one

@@ -61,13 +61,22 @@ SAN_FLAGS = ["-fsanitize=address", "-fsanitize=undefined", "-fno-omit-frame-poin
              "-fno-sanitize-recover=undefined"]
 
 
+DEBUG_OUT = os.path.join(OUT, "debug")
+DEBUG_LIB = os.path.join(DEBUG_OUT, "libgfpdot.so")
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
-          sanitize: bool = False) -> str:
+          sanitize: bool = False, debug: bool = False) -> str:
     """Compile and link libgfpdot.so; returns its path.  With sanitize=True the
     host code is built with AddressSanitizer and UndefinedBehaviorSanitizer
     into a separate library (_build/sanitize/libgfpdot.so) for host-side test
-    runs (load it with libasan preloaded); device code is unchanged."""
-    out_dir, lib = (SAN_OUT, SAN_LIB) if sanitize else (OUT, LIB)
+    runs (load it with libasan preloaded); device code is unchanged.  With
+    debug=True the kernels keep their device-side checks (GFP_DEVICE_CHECKS:
+    inputs outside the contract set error bits that gfp_context_check
+    reports) in _build/debug/libgfpdot.so."""
+    if sanitize and debug:
+        raise ValueError("one variant at a time")
+    out_dir, lib = (SAN_OUT, SAN_LIB) if sanitize else (DEBUG_OUT, DEBUG_LIB) if debug else (OUT, LIB)
     if not force and os.path.exists(lib) and all(os.path.getmtime(d) <= os.path.getmtime(lib)
                                                  for d in _deps()):
         return lib
@@ -78,6 +87,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
               "-I", CSRC]
     if sanitize:
         common += [a for f in SAN_FLAGS for a in ("-Xcompiler", f)]
+    if debug:
+        common += ["-DGFP_DEVICE_CHECKS"]
     if ptxas_info:
         common += ["-Xptxas", "-v"]
 

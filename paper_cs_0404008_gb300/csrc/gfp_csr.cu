@@ -15,6 +15,19 @@
 
 namespace gfp {
 
+#ifdef GFP_DEVICE_CHECKS
+__device__ uint32_t g_csr_check;
+uint32_t csr_check_bits()
+{
+    uint32_t h = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&h, g_csr_check, 4) != cudaSuccess) return 0;
+    cudaMemcpyToSymbol(g_csr_check, &z, 4);
+    return h;
+}
+#else
+uint32_t csr_check_bits() { return 0; }
+#endif
+
 template <class Acc>
 __global__ void __launch_bounds__(256)
     k_block_csr(Mod mod, uint64_t kbound, uint64_t m, uint64_t k, uint64_t nb,
@@ -29,6 +42,7 @@ __global__ void __launch_bounds__(256)
     for (uint64_t row = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < m;
          row += warps) {
         const uint32_t q0 = __ldg(row_ptr + row), q1 = __ldg(row_ptr + row + 1);
+        GFP_DCHECK(g_csr_check, q0 <= q1, DCHECK_CSR_ROW_PTR);
         for (uint64_t c0 = 0; c0 < nb; c0 += 64) {
             const uint64_t ca = c0 + 2 * lane;             // this lane's columns ca, ca+1
             const bool va = ca < nb, vb = ca + 1 < nb;
@@ -41,6 +55,7 @@ __global__ void __launch_bounds__(256)
                 if ((uint32_t)lane < cnt) {
                     mycol = __ldg(col + q + lane);
                     myval = __ldg(val + q + lane);
+                    GFP_DCHECK(g_csr_check, mycol < k, DCHECK_CSR_COLUMN);
                     if (mycol >= k) {   // outside the matrix: contributes nothing, reads row 0
                         mycol = 0;
                         myval = 0;
@@ -125,6 +140,7 @@ __device__ __forceinline__ void csr_row_quads(uint32_t q0, uint32_t q1, uint64_t
             cn = __ldg(col + q + 32 + lane);
             vn = __ldg(val + q + 32 + lane);
         }
+        GFP_DCHECK(g_csr_check, c < k, DCHECK_CSR_COLUMN);
         if (c >= k) {   // lanes past the end hold (0, 0)
             c = 0;
             v = 0;
@@ -161,6 +177,7 @@ __global__ void __launch_bounds__(256, PLAIN ? 4 : 3)
     const bool cvec = ((((uintptr_t)C) & 15u) == 0) && (ldc % 4 == 0);
     for (uint64_t row = (uint64_t)blockIdx.x * 8 + w; row < m; row += warps) {
         const uint32_t q0 = __ldg(row_ptr + row), q1 = __ldg(row_ptr + row + 1);
+        GFP_DCHECK(g_csr_check, q0 <= q1, DCHECK_CSR_ROW_PTR);
         for (uint64_t c0 = 0; c0 < nb; c0 += 64) {
             const uint64_t ca = c0 + 4 * (uint64_t)hl;
             const bool va = ca < nb;   // nb % 4 == 0: the whole quad is valid

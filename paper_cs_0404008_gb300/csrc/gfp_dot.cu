@@ -14,6 +14,19 @@
 
 namespace gfp {
 
+#ifdef GFP_DEVICE_CHECKS
+__device__ uint32_t g_dot_check;
+uint32_t dot_check_bits()
+{
+    uint32_t h = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&h, g_dot_check, 4) != cudaSuccess) return 0;
+    cudaMemcpyToSymbol(g_dot_check, &z, 4);
+    return h;
+}
+#else
+uint32_t dot_check_bits() { return 0; }
+#endif
+
 __device__ __forceinline__ uint4 ld_stream4(const uint4 *p) { return __ldcs(p); }
 __device__ __forceinline__ uint32_t ld_stream1(const uint32_t *p) { return __ldcs(p); }
 
@@ -163,6 +176,7 @@ __global__ void __launch_bounds__(DOT_THREADS)
         const DevUnit un = units[u];
         const DevPair pr = pairs[un.pair];
         const DevPairAux ax = aux[un.pair];
+        GFP_DCHECK(g_dot_check, un.begin <= un.end && un.end <= pr.n, DCHECK_DOT_UNIT);
         uint32_t r;
         switch (ax.repr) {
         case U64_BLOCK: r = unit_residue<AccBlock>(pr, un); break;

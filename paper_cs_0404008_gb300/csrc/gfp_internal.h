@@ -28,6 +28,29 @@ struct TraceRange {
 };
 #define GFP_TRACE() ::gfp::TraceRange gfp_trace_range_(__func__)
 
+// Device-side checks (builds with GFP_DEVICE_CHECKS only): a kernel that
+// meets an input its contract excludes, or an index outside what its launch
+// set up, records a bit in its translation unit's error word instead of
+// faulting or trapping; gfp_context_check reports the bits (GFP_ERR_INVALID)
+// and clears them.  Release builds compile the checks away.
+#ifdef GFP_DEVICE_CHECKS
+#define GFP_DCHECK(word, cond, bit)                              \
+    do {                                                          \
+        if (!(cond)) atomicOr(&(word), (uint32_t)(bit));         \
+    } while (0)
+#else
+#define GFP_DCHECK(word, cond, bit) \
+    do {                            \
+    } while (0)
+#endif
+// bits of the device-check words
+constexpr uint32_t DCHECK_CSR_COLUMN = 1u;     // a column index >= k
+constexpr uint32_t DCHECK_CSR_ROW_PTR = 2u;    // row_ptr decreases
+constexpr uint32_t DCHECK_DOT_UNIT = 4u;       // a work unit outside its pair
+// Reads and clears the words of gfp_csr.cu and gfp_dot.cu (0 in release builds).
+uint32_t csr_check_bits();
+uint32_t dot_check_bits();
+
 // One pair of a batch as the persistent kernel sees it (64 bytes).
 struct DevPair {
     const uint32_t *x;

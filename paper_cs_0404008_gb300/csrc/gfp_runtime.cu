@@ -1026,7 +1026,9 @@ GFP_API gfp_status gfp_context_check(gfp_ctx *ctx)
     if (!ctx) return GFP_ERR_INVALID;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return GFP_ERR_CUDA;
     if (cudaDeviceSynchronize() != cudaSuccess) return GFP_ERR_CUDA;
-    if (!ctx->blk_ws) return GFP_OK;
+    // device-side checks (GFP_DEVICE_CHECKS builds; always 0 otherwise)
+    const uint32_t dbits = csr_check_bits() | dot_check_bits();
+    if (!ctx->blk_ws) return dbits ? GFP_ERR_INVALID : GFP_OK;
     uint32_t *flag = block_tc_err_flag(ctx->blk_ws, ctx->blk_m, ctx->blk_k, ctx->blk_nb);
     uint32_t h = 0;
     GFP_CUDA_TRY(cudaMemcpy(&h, flag, 4, cudaMemcpyDeviceToHost));
@@ -1034,7 +1036,7 @@ GFP_API gfp_status gfp_context_check(gfp_ctx *ctx)
         GFP_CUDA_TRY(cudaMemset(ctx->blk_ws, 0, ctx->blk_ws_bytes));
         return GFP_ERR_TIMEOUT;
     }
-    return GFP_OK;
+    return dbits ? GFP_ERR_INVALID : GFP_OK;
 }
 
 GFP_API gfp_status gfp_wait_selftest(uint64_t limit_ns, void *stream)

@@ -156,13 +156,14 @@ def load(auto_build: bool = True):
     """Load the in-tree libgfpdot.so (building it first when stale).  The
     environment variable GFPDOT_SANITIZED=1 selects the host-sanitized build
     instead (AddressSanitizer and UndefinedBehaviorSanitizer in the host code;
-    the process must have libasan preloaded)."""
+    the process must have libasan preloaded), GFPDOT_DEBUG=1 the build with
+    device-side checks."""
     global _lib
     if _lib is None:
-        sanitized = os.environ.get("GFPDOT_SANITIZED") == "1"
-        path = _build.SAN_LIB if sanitized else _build.LIB
+        path = lib_path()
         if auto_build:
-            _build.build(sanitize=sanitized)
+            _build.build(sanitize=os.environ.get("GFPDOT_SANITIZED") == "1",
+                         debug=os.environ.get("GFPDOT_DEBUG") == "1")
         if not os.path.exists(path):
             raise RuntimeError(f"libgfpdot.so is missing at {path}: build it with "
                                "paper_cs_0404008_gb300.build.build()")
@@ -176,7 +177,14 @@ def load(auto_build: bool = True):
 
 
 def lib_path() -> str:
-    return _build.SAN_LIB if os.environ.get("GFPDOT_SANITIZED") == "1" else _build.LIB
+    """The library load() uses: the host-sanitized build when
+    GFPDOT_SANITIZED=1, the device-checks build when GFPDOT_DEBUG=1, else the
+    release build."""
+    if os.environ.get("GFPDOT_SANITIZED") == "1":
+        return _build.SAN_LIB
+    if os.environ.get("GFPDOT_DEBUG") == "1":
+        return _build.DEBUG_LIB
+    return _build.LIB
 
 
 def declared_symbols() -> list[str]:

@@ -32,7 +32,7 @@ def test_served_mix_matches_oracle_and_alone(lib):
     import time
 
     srv = lib.Server(device=0, mem_budget=16 << 30, n_streams=8, batch_window_us=50,
-                     max_inflight=256)
+                     max_inflight=256, block_sm_percent=50)
     try:
         specs = gi.serve_pool_specs(SEED)
         handles = {kind: [srv.register_matrix(p, side, side, seed=ms) for p, side, ms in sp]
