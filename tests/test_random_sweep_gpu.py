@@ -2,7 +2,8 @@
 edges of every bound (the Zpz and Eq. (2) thresholds, the fp16 digit range
 of the tensor cores, the FP64 eligibility limit, a delay bound of 16),
 ragged shapes, unaligned starts, every eligible representation, uniform and
-all-(p-1) operands.  Each case is compared bit for bit."""
+all-(p-1) operands; tensor-core block products also with A prepared once.
+Each case is compared bit for bit."""
 import numpy as np
 import pytest
 import torch
@@ -87,7 +88,21 @@ def test_random_block_products(lib, fresh, seed):
         assert lib.gfp_context_check(fresh) == lib.GFP_OK
         out = host(Cfull)
         assert (out[:, nb:] == 0xFFFFFFFF).all(), "wrote outside C"
-        assert np.array_equal(out[:, :nb], oracle.block(p, A, B)), (seed, case, p, tc, m, k, nb)
+        want = oracle.block(p, A, B)
+        assert np.array_equal(out[:, :nb], want), (seed, case, p, tc, m, k, nb)
+        if tc:
+            # the same product with A prepared once (any row stride), C rewritten
+            prep = lib.BlockPrep(fresh, p, dev2(A, k + int(rng.integers(0, 3))))
+            try:
+                Cfull.fill_(-1)
+                prep.matmul(fresh, dev2(B, ldb), Cfull[:, :nb])
+                torch.cuda.synchronize()
+                assert lib.gfp_context_check(fresh) == lib.GFP_OK
+                out = host(Cfull)
+                assert (out[:, nb:] == 0xFFFFFFFF).all(), "wrote outside C"
+                assert np.array_equal(out[:, :nb], want), ("prepared", seed, case, p, m, k, nb)
+            finally:
+                prep.close()
 
 
 @pytest.mark.parametrize("seed", range(16))
