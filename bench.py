@@ -440,8 +440,8 @@ def run_gpu(args):
             ln = measure_secondary(args, name, g, torch, ctx, stream)
             also[name] = {k: ln[k] for k in ("value", "unit", "ms_per_step", "config", "roofline")
                           if k in ln}
-            for k in ("single_call_us", "graph_of_256_single_dots", "same_gpu", "fields", "p_2^31-1",
-                      "prepared"):
+            for k in ("single_call_us", "graph_of_256_single_dots", "single_dot_2^27", "same_gpu",
+                      "fields", "p_2^31-1", "prepared"):
                 if k in ln:
                     also[name][k] = ln[k]
             torch.cuda.empty_cache()
@@ -694,6 +694,23 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
         e1.record()
         torch.cuda.synchronize()
         t_graph = e0.elapsed_time(e1) / reps
+        # (ii') one large single dot (2^27 elements per operand, 1 GiB, larger than L2)
+        nl = 1 << 27
+        XL = torch.empty(nl, dtype=torch.int32, device="cuda")
+        YL = torch.empty(nl, dtype=torch.int32, device="cuda")
+        g.gfp_fill_uniform(p, seed, 1000, XL)
+        g.gfp_fill_uniform(p, seed, 1001, YL)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                g.gfp_dot(ctx, p, XL, YL, out[0:1], stream)
+            e0, e1 = _events(torch, 2)
+            e0.record(stream)
+            for _ in range(10):
+                g.gfp_dot(ctx, p, XL, YL, out[0:1], stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        t_large = e0.elapsed_time(e1) / 10
+        del XL, YL
         # (iii) the same 256 dots as one persistent batched launch
         plan = g.BatchPlan(ctx, [(p, X[i], Y[i], n) for i in range(nvec)])
         ms, per = time_plan(torch, plan, out, max(10, args.steps // 10), stream)
@@ -721,6 +738,11 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                          "speedup_over_perterm": t_pt / t_batch},
             "graph_of_256_single_dots": {"ms": t_graph, "gmacs": gm(t_graph),
                                           "gbs": 8 * macs / (t_graph / 1e3) / 1e9},
+            "single_dot_2^27": {"ms": t_large, "gmacs": nl / (t_large / 1e3) / 1e9,
+                                "gbs": 8.0 * nl / (t_large / 1e3) / 1e9,
+                                "frac": 8.0 * nl / (t_large / 1e3) / 1e9 / peak,
+                                "what": "one gfp_dot call over 2^27-element operands (1 GiB), "
+                                        "back to back, L2-cold"},
             "roofline": with_read_peak(
                 {"bound": "hbm", "achieved": 8 * macs / (t_batch / 1e3) / 1e9, "peak": peak,
                  "unit": "GB/s", "frac": 8 * macs / (t_batch / 1e3) / 1e9 / peak,
