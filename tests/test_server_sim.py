@@ -144,3 +144,32 @@ def test_memory_budget_from_environment(lib, monkeypatch):
         assert st == lib.GFP_ERR_NOMEM
     finally:
         s.close()
+
+
+def test_prepare_matrix_in_simulation(lib, srv_factory):
+    """gfp_prepare_matrix: a no-op in simulation mode for a known matrix,
+    GFP_ERR_INVALID for an unknown handle; block jobs still complete."""
+    s = srv_factory()
+    h = s.register_matrix(65521, 256, 256, seed=9)
+    s.prepare_matrix(h)
+    s.prepare_matrix(h)   # preparing twice is allowed
+    with pytest.raises(lib.GfpError) as ei:
+        s.prepare_matrix(h + 1000)
+    assert ei.value.status == lib.GFP_ERR_INVALID
+    t = s.submit(lib.GFP_JOB_BLOCK, 65521, matrix=h, nb=64, seed=3)
+    st, r = s.wait(t, 2_000_000)
+    assert st == lib.GFP_OK and r.status == lib.GFP_OK
+
+
+def test_block_sm_share_and_priority_streams_accepted(lib, srv_factory):
+    """The block-SM share and the stream split are accepted in any range; a
+    one-stream pool runs every kind on its single stream."""
+    for pct, ns in ((0, 1), (50, 2), (100, 3), (150, 8)):
+        s = srv_factory(block_sm_percent=pct, n_streams=ns)
+        h = s.register_matrix(65521, 128, 128, seed=1)
+        ts = [s.submit(lib.GFP_JOB_DOT, 65521, n=1000, seed=2),
+              s.submit(lib.GFP_JOB_MATVEC, 65521, matrix=h, seed=3),
+              s.submit(lib.GFP_JOB_BLOCK, 65521, matrix=h, nb=64, seed=4)]
+        for t in ts:
+            st, r = s.wait(t, 2_000_000)
+            assert st == lib.GFP_OK and r.status == lib.GFP_OK, (pct, ns)
