@@ -13,6 +13,7 @@
 namespace gfp {
 
 constexpr int MV_RB = 64;   // rows per batch (multiple of every group count G)
+constexpr int MV_PREFETCH_ROWS = 4;   // rows of A requested into L2 before the dependency wait
 
 // Sum of one uint64 per thread over the CTA, valid in thread 0.
 __device__ __forceinline__ uint64_t cta_sum_mv(uint64_t v)
@@ -51,6 +52,22 @@ __global__ void __launch_bounds__(MV_THREADS, 1)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     const uint64_t colsp = (cols + 3) & ~3ull;
+    // Programmatic dependent launch: the next kernel of the stream may be
+    // scheduled on SMs this grid has left (its tail).  A never changes, so
+    // before waiting for the previous kernel (which may have produced x) the
+    // CTA asks L2 for the first rows it will stream; everything that reads
+    // x or writes y comes after the wait.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    {
+        const uint64_t r0 = rows * blockIdx.x / gridDim.x, r1 = rows * (blockIdx.x + 1) / gridDim.x;
+        const uint64_t row_bytes = cols * 4;
+        if (threadIdx.x < MV_PREFETCH_ROWS && r0 + threadIdx.x < r1 &&
+            ((((uintptr_t)A) | (lda * 4) | row_bytes) & 15u) == 0 && row_bytes <= 0xFFFFFFF0ull)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(A + (r0 + threadIdx.x) * lda),
+                         "r"((uint32_t)row_bytes)
+                         : "memory");
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     uint32_t *xs = smem;
     uint32_t *part = smem + (XS ? colsp : 0);
     const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -158,9 +175,19 @@ static cudaError_t mv_launch(const Mod &m, uint64_t k, uint64_t rows, uint64_t c
     }
     uint64_t grid = (uint64_t)sm_count;
     if (grid > rows) grid = rows ? rows : 1;
-    k_matvec<Acc, XS, U><<<(unsigned)grid, MV_THREADS, smem, s>>>(m, k, rows, cols, A, lda, x, y,
-                                                                  W, proj);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(MV_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_matvec<Acc, XS, U>, m, k, rows, cols, A, lda, x,
+                                             y, W, proj);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <class Acc>
