@@ -168,25 +168,6 @@ __global__ void __launch_bounds__(DOT_THREADS)
                   uint32_t *__restrict__ out)
 {
     __shared__ uint32_t s_u;
-    // Programmatic dependent launch: this grid's CTAs may be placed while the
-    // previous kernel of the stream drains.  Before waiting on it, a CTA asks
-    // L2 for the operands of unit blockIdx.x (units are taken largest first,
-    // so the first grid-full are the ones the CTAs will take); descriptors and
-    // work list were written before the previous kernel (a plan) or by copies
-    // just before this launch, which this kernel is ordered after as usual.
-    // The work counters and outputs are touched only after the wait.
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    if (threadIdx.x < 2 && blockIdx.x < n_units) {
-        const DevUnit un = units[blockIdx.x];
-        const DevPair pr = pairs[un.pair];
-        const uint32_t *v = threadIdx.x ? pr.y : pr.x;
-        const uint64_t bytes = (un.end - un.begin) * 4;
-        const uintptr_t a = (uintptr_t)(v + un.begin);
-        if (bytes >= 16 && bytes <= 0xFFFFFFF0ull && ((a | bytes) & 15u) == 0)
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)bytes)
-                         : "memory");
-    }
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (;;) {
         if (threadIdx.x == 0) s_u = atomicAdd(&sc.ctr[0], 1u);
         __syncthreads();
@@ -343,17 +324,8 @@ cudaError_t launch_dot_batched(const DevPair *pairs, const DevPairAux *aux, cons
                                uint32_t n_units, BatchScratch sc, uint32_t *out, int grid,
                                cudaStream_t s)
 {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(DOT_THREADS);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_dot_batched, pairs, aux, units, n_units, sc, out);
-    return e != cudaSuccess ? e : cudaGetLastError();
+    k_dot_batched<<<grid, DOT_THREADS, 0, s>>>(pairs, aux, units, n_units, sc, out);
+    return cudaGetLastError();
 }
 
 static uint64_t fill_key(uint64_t seed, uint64_t stream_id)
