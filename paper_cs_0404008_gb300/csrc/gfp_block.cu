@@ -355,6 +355,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
     } else if (warp == W_BPROD) {
         // ---------------- producer: B digit tiles (bulk copies from the prepared image) ----------------
         if (lane == 0) {
+            // the image is written by the B-digit kernel launched just before
+            // this one (programmatic dependent launch): the only read of its
+            // output, so the only role that waits for it; A's copies, barrier
+            // set-up and TMEM allocation overlap its run
+            asm volatile("griddepcontrol.wait;" ::: "memory");
             int armed[BSTAGES];
             for (int s = 0; s < BSTAGES; ++s) armed[s] = -1;
             uint32_t it = 0;
@@ -587,6 +592,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
 __global__ void k_block_prep_b(const uint32_t *B, uint64_t ldb, uint64_t k, uint64_t nb, Mod mod,
                                uint32_t half, uint32_t kblocks, int pre, uint8_t *img)
 {
+    // the product kernel that follows may be placed now (it waits for this
+    // grid only where it reads the image)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const uint32_t tile = blockIdx.x;            // nt * kblocks + kb
     const uint32_t nt = tile / kblocks, kb = tile % kblocks;
     uint8_t *out = img + (uint64_t)tile * B_TILE_BYTES;
@@ -942,12 +950,26 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint64_t grid = std::min<uint64_t>(a.units, (uint64_t)sm_count);
-    if (Aimg)   // the image already holds the residues of this pass's modulus
-        k_block_tc<false, true, PipePrep><<<(unsigned)grid, THREADS, PipePrep::SMEM_BYTES, s>>>(a);
-    else if (reduce_inputs)
-        k_block_tc<true, false, PipeU32><<<(unsigned)grid, THREADS, PipeU32::SMEM_BYTES, s>>>(a);
-    else
-        k_block_tc<false, false, PipeU32><<<(unsigned)grid, THREADS, PipeU32::SMEM_BYTES, s>>>(a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl;
+    cfg.numAttrs = 1;
+    if (Aimg) {   // the image already holds the residues of this pass's modulus
+        cfg.dynamicSmemBytes = PipePrep::SMEM_BYTES;
+        e = cudaLaunchKernelEx(&cfg, k_block_tc<false, true, PipePrep>, a);
+    } else if (reduce_inputs) {
+        cfg.dynamicSmemBytes = PipeU32::SMEM_BYTES;
+        e = cudaLaunchKernelEx(&cfg, k_block_tc<true, false, PipeU32>, a);
+    } else {
+        cfg.dynamicSmemBytes = PipeU32::SMEM_BYTES;
+        e = cudaLaunchKernelEx(&cfg, k_block_tc<false, false, PipeU32>, a);
+    }
+    if (e != cudaSuccess) return e;
     *launches += 2;
     return cudaGetLastError();
 }
