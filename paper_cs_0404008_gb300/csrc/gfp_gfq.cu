@@ -160,9 +160,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     __shared__ uint32_t wpart[THREADS / 32];
     __shared__ uint32_t last;
     // Z[0 .. qbar] is all the arithmetic of valid codes reads
+    // programmatic dependent launch: placed while the previous kernel of the
+    // stream drains, a CTA loads the field's table (constant) first and only
+    // then waits for that kernel, which may have produced the codes
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const uint32_t nload = (qbar + 8u) / 8u;
     for (uint32_t i = threadIdx.x; i < nload; i += blockDim.x)
         reinterpret_cast<uint4 *>(Z)[i] = reinterpret_cast<const uint4 *>(Zg)[i];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     __syncthreads();
 
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -239,9 +244,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     extern __shared__ uint16_t E[];
     __shared__ unsigned long long wpart[THREADS / 32];
     __shared__ uint32_t last;
+    // programmatic dependent launch: placed while the previous kernel of the
+    // stream drains, a CTA loads the field's table (constant) first and only
+    // then waits for that kernel, which may have produced the codes
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const uint32_t nload = (qbar + 8u) / 8u;   // E[0 .. qbar]
     for (uint32_t i = threadIdx.x; i < nload; i += blockDim.x)
         reinterpret_cast<uint4 *>(E)[i] = reinterpret_cast<const uint4 *>(Eg)[i];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     __syncthreads();
 
     // value of the product of codes a and b (0 if either is the zero element)
@@ -336,8 +346,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     extern __shared__ uint8_t T[];
     __shared__ uint32_t wpart[THREADS / 32];
     __shared__ uint32_t last;
+    // programmatic dependent launch: placed while the previous kernel of the
+    // stream drains, a CTA loads the field's table (constant) first and only
+    // then waits for that kernel, which may have produced the codes
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     for (uint32_t i = threadIdx.x; i < tbytes / 16u; i += blockDim.x)
         reinterpret_cast<uint4 *>(T)[i] = reinterpret_cast<const uint4 *>(Tg)[i];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     __syncthreads();
     const uint8_t *E = T, *ADD = T + 256;
 
@@ -700,22 +715,38 @@ GFP_API gfp_status gfp_gfq_dot(gfp_gfq *fq, uint64_t n, const uint16_t *x, const
     const uint64_t work = vec ? (n + 7) / 8 : n;
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)fq->grid,
                                                                     (work + gfq::THREADS - 1) / gfq::THREADS));
-    if (fq->mode == 1)
-        gfq::k_gfq_dot_exp<false><<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_exp16, fq->qbar, fq->p,
-                                                                         fq->d_log, fq->d_acc, fq->d_ticket, out);
-    else if (fq->mode == 2)
-        gfq::k_gfq_dot_exp<true><<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_exp16, fq->qbar, fq->p,
-                                                                        fq->d_log, fq->d_acc, fq->d_ticket, out);
-    else if (fq->mode == 3)
-        gfq::k_gfq_dot_add<<<grid, gfq::THREADS, fq->tab8_bytes, s>>>(x, y, n, vec, fq->d_tab8, fq->tab8_bytes,
-                                                                       fq->q, fq->qbar, fq->d_log, fq->d_partials,
-                                                                       fq->d_ticket, out);
-    else if (fq->q >= gfq::RARE_Q)
-        gfq::k_gfq_dot<true><<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_zech, fq->qbar,
-                                                                    fq->d_partials, fq->d_ticket, out);
-    else
-        gfq::k_gfq_dot<false><<<grid, gfq::THREADS, gfq::SMEM, s>>>(x, y, n, vec, fq->d_zech, fq->qbar,
-                                                                     fq->d_partials, fq->d_ticket, out);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(gfq::THREADS);
+    cfg.dynamicSmemBytes = gfq::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute pdl[1];
+    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl;
+    cfg.numAttrs = 1;
+    if (fq->mode == 1) {
+        GFQ_TRY(cudaLaunchKernelEx(&cfg, gfq::k_gfq_dot_exp<false>, x, y, n, vec,
+                                   (const uint16_t *)fq->d_exp16, fq->qbar, fq->p,
+                                   (const uint32_t *)fq->d_log, fq->d_acc, fq->d_ticket, out));
+    } else if (fq->mode == 2) {
+        GFQ_TRY(cudaLaunchKernelEx(&cfg, gfq::k_gfq_dot_exp<true>, x, y, n, vec,
+                                   (const uint16_t *)fq->d_exp16, fq->qbar, fq->p,
+                                   (const uint32_t *)fq->d_log, fq->d_acc, fq->d_ticket, out));
+    } else if (fq->mode == 3) {
+        cfg.dynamicSmemBytes = fq->tab8_bytes;
+        GFQ_TRY(cudaLaunchKernelEx(&cfg, gfq::k_gfq_dot_add, x, y, n, vec, (const uint8_t *)fq->d_tab8,
+                                   (uint32_t)fq->tab8_bytes, (uint32_t)fq->q, fq->qbar,
+                                   (const uint32_t *)fq->d_log, fq->d_partials, fq->d_ticket, out));
+    } else if (fq->q >= gfq::RARE_Q) {
+        GFQ_TRY(cudaLaunchKernelEx(&cfg, gfq::k_gfq_dot<true>, x, y, n, vec,
+                                   (const uint16_t *)fq->d_zech, fq->qbar, fq->d_partials,
+                                   fq->d_ticket, out));
+    } else {
+        GFQ_TRY(cudaLaunchKernelEx(&cfg, gfq::k_gfq_dot<false>, x, y, n, vec,
+                                   (const uint16_t *)fq->d_zech, fq->qbar, fq->d_partials,
+                                   fq->d_ticket, out));
+    }
     GFQ_TRY(cudaGetLastError());
     return GFP_OK;
 }
