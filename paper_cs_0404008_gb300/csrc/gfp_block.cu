@@ -61,26 +61,10 @@ constexpr int A_TILE_BYTES = BM * BK * 4;                     // 32 KiB of uint3
 constexpr int A_DIGIT_BYTES = BM * BK * 2;                    // 16 KiB per digit
 constexpr int B_TILE_BYTES = MMA_N * BK * 2;                  // 16 KiB
 static_assert(A_TILE_BYTES == 2 * A_DIGIT_BYTES, "in-place conversion needs equal sizes");
-// Warp roles, in warpgroups of four: warpgroup 0 holds the A producer, the
-// MMA issuer and the B producer (its fourth warp is idle), warpgroups 1-4 the
-// sixteen converter warps, warpgroup 5 the four epilogue warps.  The kernel is
-// launched with REG_LAUNCH registers per thread; the converters then give
-// back REG_LAUNCH - REG_CONV each and the epilogue takes exactly that pool
-// (setmaxnreg), so that the epilogue's 64 residue sums stay in registers:
-// 16 * 32 * (80 - 64) = 4 * 32 * (144 - 80).  The host refuses to launch if
-// ptxas compiled the kernel to any other register count (a split that asks
-// for more than was released would wait forever).
-constexpr int CONV_WARPS = 16;
-constexpr int CONV_THREADS = 32 * CONV_WARPS;
+constexpr int CONV_WARPS = 8;
 constexpr int EPI_WARPS = 4;
-constexpr int W_APROD = 0, W_MMA = 1, W_BPROD = 2, W_CONV0 = 4, W_EPI0 = W_CONV0 + CONV_WARPS;
-constexpr int THREADS = 32 * (W_EPI0 + EPI_WARPS);            // 768
-constexpr int REG_LAUNCH = 80, REG_CONV = 64, REG_EPI = 144;
-static_assert(CONV_WARPS * (REG_LAUNCH - REG_CONV) == EPI_WARPS * (REG_EPI - REG_LAUNCH),
-              "the epilogue takes exactly what the converters release");
-static_assert(THREADS * REG_LAUNCH <= 65536, "registers per SM");
-constexpr int NCH = (BM * BK / 4) / CONV_THREADS;   // 16-byte chunks per converter thread per k-block
-static_assert(NCH * CONV_THREADS == BM * BK / 4, "chunks divide evenly");
+constexpr int W_APROD = 0, W_MMA = 1, W_BPROD = 2, W_CONV0 = 3, W_EPI0 = W_CONV0 + CONV_WARPS;
+constexpr int THREADS = 32 * (W_EPI0 + EPI_WARPS);            // 480
 constexpr uint32_t TMEM_COLS = 512;   // 2 accumulator sets x 2 digits x 128 columns
 constexpr uint64_t WAIT_NS = 2000000000ull;   // bounded waits: 2 s
 constexpr uint32_t IDESC = ptx::idesc_f16_f32(BM, MMA_N);
@@ -228,7 +212,7 @@ __device__ __forceinline__ void split_pair(uint32_t a0, uint32_t a1, uint32_t p,
 // overwrites the same 32 KiB with the two 128-byte-swizzled K-major fp16
 // digit tiles (high digits first).
 struct ARegs {
-    uint4 v[NCH];
+    uint4 v[8];
 };
 
 // sub-tile `sub` of a slot holding KBB k-blocks (row stride BK*4*KBB bytes)
@@ -236,8 +220,8 @@ template <int KBB>
 __device__ __forceinline__ void load_tile(const uint8_t *slot, int sub, int ct, ARegs &r)
 {
 #pragma unroll
-    for (int i = 0; i < NCH; ++i) {
-        const int q = ct + CONV_THREADS * i;
+    for (int i = 0; i < 8; ++i) {
+        const int q = ct + 256 * i;
         const int row = q >> 4, c4 = q & 15;
         r.v[i] = *reinterpret_cast<const uint4 *>(slot + row * (BK * 4 * KBB) + sub * (BK * 4) + c4 * 16);
     }
@@ -257,8 +241,8 @@ __device__ __forceinline__ void store_digits(const Args &a, const ARegs &r, uint
     uint8_t *th = stage;                    // high digits
     uint8_t *tl = stage + A_DIGIT_BYTES;    // low digits
 #pragma unroll
-    for (int i = 0; i < NCH; ++i) {
-        const int q = ct + CONV_THREADS * i;
+    for (int i = 0; i < 8; ++i) {
+        const int q = ct + 256 * i;
         const int row = q >> 4, c4 = q & 15;
         uint32_t h01, l01, h23, l23;
         uint4 w = r.v[i];
@@ -462,14 +446,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                    ptx::globaltimer() - t0 < WAIT_NS) {
             }
         }
-    } else if (PREP && warp >= W_CONV0 && warp < W_EPI0) {
+    } else if (PREP && warp < W_EPI0) {
         // prepared digits need no conversion: the converter warps stand by
-        // (after releasing their registers to the epilogue, as below)
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_CONV));
-    } else if (warp >= W_CONV0 && warp < W_EPI0) {
+    } else if (warp < W_EPI0) {
         // ---------------- converters: uint32 tiles -> centred fp16 digits, in place ----------------
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_CONV));
-        const int ct = threadIdx.x - 32 * W_CONV0;   // 0..CONV_THREADS-1
+        const int ct = threadIdx.x - 32 * W_CONV0;   // 0..255
         uint32_t si = 0;
         for (uint64_t u = u0; u < u1; ++u) {
             const UnitPos q = unit_pos(a, u);
@@ -498,9 +479,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
             }
             if (!ok) break;
         }
-    } else if (warp >= W_EPI0) {
+    } else {
         // ---------------- epilogue: TMEM -> residues ----------------
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_EPI));
         const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31
         const int row_in_tile = quarter * 32 + lane;
         const uint32_t lane_bits = (uint32_t)(quarter * 32) << 16;
@@ -920,17 +900,6 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
             e = cudaFuncSetAttribute(k_block_tc<false, true, PipePrep>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipePrep::SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        // the register split inside the kernel balances only at REG_LAUNCH
-        // registers per thread: refuse to launch a build compiled otherwise
-        const void *kernels[3] = {(const void *)k_block_tc<false, false, PipeU32>,
-                                  (const void *)k_block_tc<true, false, PipeU32>,
-                                  (const void *)k_block_tc<false, true, PipePrep>};
-        for (const void *k : kernels) {
-            cudaFuncAttributes fa;
-            e = cudaFuncGetAttributes(&fa, k);
-            if (e != cudaSuccess) return e;
-            if (fa.numRegs != REG_LAUNCH) return cudaErrorInvalidConfiguration;
-        }
         attr = true;
     }
     Args a;
