@@ -880,19 +880,21 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                 "same_gpu": {n: {"ms": v, "gmacs": macs / (v / 1e3) / 1e9} for n, v in res.items()},
                 "gpu_launches": 2 if passes == 1 else 2 * passes + 1,
             })
-            pbytes = prep_bytes + passes * 4.0 * k * nb + 4.0 * m * nb
-            if passes > 1:
-                pbytes += 2 * passes * 4.0 * m * nb
+            ppasses = rns_passes(p, k, 65536)
+            pbytes = prep_bytes + ppasses * 4.0 * k * nb + 4.0 * m * nb
+            if ppasses > 1:
+                pbytes += 2 * ppasses * 4.0 * m * nb
             pach = pbytes / (t_prep / 1e3) / 1e9
             line["prepared"] = {
                 "ms": t_prep, "gmacs": macs / (t_prep / 1e3) / 1e9, "passes": prep_passes,
-                "what": "A prepared once into fp16 digit images (4 bytes per entry per pass), "
-                        "then one product per call (B digits + tensor-core kernel)",
+                "what": "A prepared once into 8-bit digit planes (2 bytes per entry per pass), "
+                        "then one product per call (B digits + tensor-core kernel widening "
+                        "A's digits in shared memory)",
                 "roofline": with_read_peak({"bound": "hbm", "achieved": pach, "peak": peak,
                                             "unit": "GB/s", "frac": pach / peak,
                                             "kernel": "k_block_tc (prepared A) + k_block_prep_b",
                                             "traffic": (traffic_for("k_block_tc_prepared", pbytes)
-                                                        if passes == 1 else None),
+                                                        if ppasses == 1 else None),
                                             "peak_kind": f"{peak_kind} hbm_gbs"})}
             if large:
                 line["p_2^31-1"] = {n: {"ms": v, "gmacs": macs / (v / 1e3) / 1e9} for n, v in large.items()}
@@ -1160,13 +1162,14 @@ SWEEP_PAPER_PRIMES_32 = [2887, 2897, 2903, 32749, 40009, 40499, 46337, 65521]
 SWEEP_PAPER_PRIMES_64 = [94906249, 2147483647, 3037000493, 4294967291]
 
 
-def rns_passes(p: int, k: int) -> int:
+def rns_passes(p: int, k: int, direct_max: int = 65791) -> int:
     """Tensor-core passes of a k-deep block product over GF(p): one for
-    p <= 65791, else the number of largest primes <= 65791 whose product
-    exceeds k (p-1)^2 (the residue moduli the library picks)."""
-    if p <= 65791:
+    p <= direct_max (65791 for uint32 A, 65536 for a prepared A), else the
+    number of largest primes <= 65536 whose product exceeds k (p-1)^2 (the
+    residue moduli the library picks)."""
+    if p <= direct_max:
         return 1
-    bound, prod, count, c = k * (p - 1) ** 2, 1, 0, 65791
+    bound, prod, count, c = k * (p - 1) ** 2, 1, 0, 65536
     while prod <= bound:
         while not is_prime(c):
             c -= 1

@@ -76,7 +76,7 @@ typedef enum gfp_repr {
     GFP_REPR_F16TC = 5,     /* block product only: centred residues (Section 3.2.2) split into
                                two balanced 8-bit digits, exact fp16 tensor-core products with
                                fp32 accumulation over chunks of 1024 terms (p <= 65791; larger
-                               p through residues modulo primes <= 65791) */
+                               p through residues modulo primes <= 65536) */
     GFP_REPR_CENTERED = 6,  /* centred representation (Section 3.2.2): signed residues in
                                [-(p-1)/2, (p-1)/2], signed 64-bit accumulator reduced every
                                k terms, k h^2 + (p-1) <= 2^63 - 1 with h = (p-1)/2 */
@@ -262,7 +262,7 @@ GFP_API gfp_status gfp_matvec_sequence(gfp_ctx *ctx, uint32_t p, uint64_t n, con
  * multiple of 4, the tensor cores: for p <= 65791 the digit kernel directly
  * (two launches: B digit split, then the persistent product); for larger p
  * one such pass per modulus of a residue number system (the L <= 6 largest
- * primes <= 65791 whose product exceeds k (p-1)^2, each pass reducing the
+ * primes <= 65536 whose product exceeds k (p-1)^2, each pass reducing the
  * inputs modulo its prime) and one launch recombining the residues with
  * Garner's method modulo p.  Otherwise the CUDA-core kernel with the
  * representation forced on the context, else the built-in rule for p (tuned
@@ -277,13 +277,14 @@ GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64
 
 /* A prepared once for repeated block products with the same A (block
  * Wiedemann-style iterations, a resident matrix serving many requests): the
- * centred residues of Section 3.2.2 split into the two balanced 8-bit digits
- * the tensor-core product uses (see gfp_matmul_block), stored as fp16 digit
- * tiles in the layout its matrix units read, so that each product copies
- * them as they are, with no per-call conversion.  For p <= 65791 one image of
- * 4 bytes per entry of A; for larger p one image per residue-pass modulus
- * (A reduced modulo each), 4 bytes per entry each (gfp_block_prep_info gives
- * the bytes and the pass count).
+ * residues of A split once into the two balanced 8-bit digits the tensor-core
+ * product multiplies (the centred representation of Section 3.2.2, with the
+ * representative of each residue taken in [-32896, 32639] so that both
+ * digits fit a byte), stored as two 8-bit digit planes per tile, 2 bytes per
+ * entry of A: each product reads half the bytes of the uint32 A and only
+ * widens the digits to fp16 in shared memory.  For p <= 65536 one image; for
+ * larger p one image per residue-pass modulus (A reduced modulo each, 2 bytes
+ * per entry each; gfp_block_prep_info gives the bytes and the pass count).
  *   A: device, m x k row-major, lda >= k, canonical residues; not referenced
  *   after the call returns (it synchronises the device).  m, k >= 1.
  * GFP_ERR_UNSUPPORTED when no residue passes cover k (p-1)^2; GFP_ERR_NOMEM
@@ -301,7 +302,7 @@ GFP_API gfp_status gfp_block_prepare(gfp_ctx *ctx, uint32_t p, uint64_t m, uint6
 GFP_API gfp_status gfp_matmul_block_prepared(gfp_ctx *ctx, const gfp_block_prep *prep, uint64_t nb,
                                              const uint32_t *B, uint64_t ldb, uint32_t *C,
                                              uint64_t ldc, void *stream);
-/* Device bytes held and residue passes per product (1 for p <= 65791). */
+/* Device bytes held and residue passes per product (1 for p <= 65536). */
 GFP_API gfp_status gfp_block_prep_info(const gfp_block_prep *prep, uint64_t *bytes,
                                        uint32_t *passes);
 /* Synchronises the device and frees the prepared images. */

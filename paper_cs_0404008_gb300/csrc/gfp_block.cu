@@ -30,7 +30,7 @@
 //
 // Larger moduli on the tensor cores (p > 65791): the exact integer products
 // sum_t A[i][t] B[t][j] are below k (p-1)^2, so they are fixed by their
-// residues modulo a few small primes p' <= 65791 whose product exceeds that
+// residues modulo a few small primes p' <= 65536 whose product exceeds that
 // bound (a residue number system).  Each pass runs the tensor-core kernel
 // above modulo one p', reducing every input a < 2^32 to a mod p' while it is
 // split into digits; a last kernel recombines the residues with Garner's
@@ -99,13 +99,25 @@ struct Pipe {
     static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 };
 using PipeU32 = Pipe<3, 2, 2>;    // uint32 A, converted in place
-using PipePrep = Pipe<4, 4, 1>;   // prepared A digits
+using PipePrep = Pipe<4, 4, 1>;   // prepared A: 8-bit digit planes, widened in place
+static_assert(PipePrep::KBB == 1, "one prepared tile per slot");
+
+// Prepared A (gfp_block_prepare): per (m-tile, k-block) two planes of 8-bit
+// digits, high then low, each 128 rows x 64 K, row-major, every digit stored
+// with a bias of 128.  A residue a of p <= 65536 is represented by s = a or
+// a - p in [-32896, 32639] (s = a when a <= min((p-1)/2, 32639)), split as
+// s = 256 h + l with h, l in [-128, 127]: u = s + 32896 in [0, 65535] holds
+// h + 128 in its high byte and l + 128 in its low byte.  Every digit is still
+// at most 128 in magnitude, so the 1024-term fp32 chunks stay exact.
+constexpr int A8_PLANE_BYTES = BM * BK;           // 8 KiB per digit plane
+constexpr int A8_TILE_BYTES = 2 * A8_PLANE_BYTES; // 16 KiB per (m-tile, k-block)
+constexpr uint32_t DIGIT8_MAX_P = 65536;
 
 struct Args {
     CUtensorMap tmap_a;       // A as a 2-D uint32 tensor {k, m}, box {BK*KBB, BM} (uint32 pipe), zero fill
     uint64_t m, k, nb;
     const uint8_t *Bimg;      // [n_tiles][kblocks] tiles of B_TILE_BYTES
-    const uint8_t *Aimg;      // prepared A: [m_tiles][kblocks] digit tiles of A_TILE_BYTES (PREP)
+    const uint8_t *Aimg;      // prepared A: [m_tiles][kblocks] tiles of A8_TILE_BYTES (PREP)
     uint32_t *C;
     uint64_t ldc;
     uint32_t *Cacc;           // m x (n_tiles*NT) u32 partial residue sums (zero outside calls)
@@ -262,10 +274,38 @@ __device__ __forceinline__ void store_digits(const Args &a, const ARegs &r, uint
     }
 }
 
+// A prepared tile's 16-byte chunk c of 1024 (thread ct takes c = ct + 256 i):
+// plane c / 512, row (c / 4) mod 128, K columns 16 (c mod 4) .. + 15.  Its
+// 16 biased bytes become 16 fp16 digits: the fp16 encoding of 1408 + b for a
+// byte b is the 16-bit integer 0x6580 + b, and one exact subtraction of 1536
+// leaves b - 128.  The two 8-digit halves land at their 128-byte-swizzled
+// places of the plane's fp16 tile (high digits at slot offset 0, low at
+// A_DIGIT_BYTES), the layout the MMAs read.
+__device__ __forceinline__ void widen_store(uint8_t *slot, int c, uint4 w)
+{
+    const int d = c >> 9, row = (c >> 2) & 127, j = c & 3;
+    const __half2 bias = __halves2half2(__ushort_as_half(0x6600), __ushort_as_half(0x6600));
+    const uint32_t in[4] = {w.x, w.y, w.z, w.w};
+    uint32_t o[8];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const uint32_t b01 = __byte_perm(in[e], 0u, 0x4140) + 0x65806580u;   // bytes 0, 1
+        const uint32_t b23 = __byte_perm(in[e], 0u, 0x4342) + 0x65806580u;   // bytes 2, 3
+        const __half2 h01 = __hsub2(*reinterpret_cast<const __half2 *>(&b01), bias);
+        const __half2 h23 = __hsub2(*reinterpret_cast<const __half2 *>(&b23), bias);
+        o[2 * e] = *reinterpret_cast<const uint32_t *>(&h01);
+        o[2 * e + 1] = *reinterpret_cast<const uint32_t *>(&h23);
+    }
+    uint8_t *tile = slot + (size_t)d * A_DIGIT_BYTES;
+    const uint32_t r7 = (uint32_t)(row & 7), base = (uint32_t)row * 128u;
+    *reinterpret_cast<uint4 *>(tile + base + (((uint32_t)(2 * j) ^ r7) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
+    *reinterpret_cast<uint4 *>(tile + base + (((uint32_t)(2 * j + 1) ^ r7) << 4)) = make_uint4(o[4], o[5], o[6], o[7]);
+}
+
 // PRE: reduce each input modulo p while splitting it (the residue passes).
-// PREP: A arrives already centred and split, as digit tiles in the exact
-// shared-memory layout (a prepared operand, see k_block_prep_a); the
-// producer bulk-copies whole slots and the converter warps have no work.
+// PREP: A arrives prepared, as 8-bit digit planes (k_block_prep_a); the
+// producer bulk-copies a 16 KiB tile into the upper half of a slot and the
+// converter warps widen it in place into the two fp16 digit tiles.
 template <bool PRE, bool PREP, class P>
 __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__ Args a)
 {
@@ -330,11 +370,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                     }
                     const uint32_t fb = ptx::smem_u32(&bars->a_full[s]);
                     if (PREP) {
-                        // the slot's k-blocks are consecutive tiles of the image
-                        const uint32_t bytes = min((uint32_t)KBB, q.kb1 - kb) * (uint32_t)A_TILE_BYTES;
-                        ptx::mbar_arrive_expect_tx(fb, bytes);
-                        ptx::bulk_g2s(ptx::smem_u32(slot_mem + (size_t)s * SLOT_BYTES),
-                                      a.Aimg + ((uint64_t)q.mt * a.kblocks + kb) * A_TILE_BYTES, bytes, fb);
+                        // one prepared tile, into the slot's upper half
+                        ptx::mbar_arrive_expect_tx(fb, A8_TILE_BYTES);
+                        ptx::bulk_g2s(ptx::smem_u32(slot_mem + (size_t)s * SLOT_BYTES + A_DIGIT_BYTES),
+                                      a.Aimg + ((uint64_t)q.mt * a.kblocks + kb) * A8_TILE_BYTES,
+                                      A8_TILE_BYTES, fb);
                     } else {
                         ptx::mbar_arrive_expect_tx(fb, SLOT_BYTES);
                         ptx::tma_load_2d(ptx::smem_u32(slot_mem + (size_t)s * SLOT_BYTES), &a.tmap_a,
@@ -410,10 +450,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                     const uint32_t sub = (kb - q.kb0) % KBB;
                     const uint32_t s = si % SLOTS, round = si / SLOTS;
                     const uint32_t sb = it % BSTAGES, roundb = it / BSTAGES;
-                    // the slot's digits: converted in place, or landed ready-made (PREP)
-                    const uint32_t abar = PREP ? ptx::smem_u32(&bars->a_full[s]) : ptx::smem_u32(&bars->conv[s]);
+                    // the slot's fp16 digits: converted or widened in place
                     if (!wait_bar(ptx::smem_u32(&bars->full_b[sb]), roundb & 1, abort, a.err) ||
-                        (sub == 0 && !wait_bar(abar, round & 1, abort, a.err))) {
+                        (sub == 0 && !wait_bar(ptx::smem_u32(&bars->conv[s]), round & 1, abort, a.err))) {
                         ok = false;
                         break;
                     }
@@ -447,7 +486,34 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
             }
         }
     } else if (PREP && warp < W_EPI0) {
-        // prepared digits need no conversion: the converter warps stand by
+        // ---------------- converters: 8-bit digit planes -> fp16 digit tiles, in place ----------------
+        const int ct = threadIdx.x - 32 * W_CONV0;   // 0..255
+        uint32_t si = 0;
+        for (uint64_t u = u0; u < u1; ++u) {
+            const UnitPos q = unit_pos(a, u);
+            bool ok = true;
+            for (uint32_t kb = q.kb0; kb < q.kb1; ++kb, ++si) {
+                const uint32_t s = si % SLOTS, round = si / SLOTS;
+                const bool got = warp_wait(ptx::smem_u32(&bars->a_full[s]), round & 1, abort, a.err);
+                // every converter warp reads its chunks before any overwrites them
+                if (ptx::bar_red_or<2, CONV_WARPS * 32>(!got || *abort != 0)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t *slot = slot_mem + (size_t)s * SLOT_BYTES;
+                const uint4 *src = reinterpret_cast<const uint4 *>(slot + A_DIGIT_BYTES);
+                uint4 w[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) w[i] = src[ct + 256 * i];
+                asm volatile("bar.sync 2, %0;" ::"n"(CONV_WARPS * 32) : "memory");
+#pragma unroll
+                for (int i = 0; i < 4; ++i) widen_store(slot, ct + 256 * i, w[i]);
+                ptx::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&bars->conv[s]));
+            }
+            if (!ok) break;
+        }
     } else if (warp < W_EPI0) {
         // ---------------- converters: uint32 tiles -> centred fp16 digits, in place ----------------
         const int ct = threadIdx.x - 32 * W_CONV0;   // 0..255
@@ -620,35 +686,34 @@ __global__ void k_block_prep_b(const uint32_t *B, uint64_t ldb, uint64_t k, uint
 }
 
 // A (m x k, row-major uint32 residues, leading dimension lda) -> prepared
-// digit image for one modulus: per (m-tile, k-block) one tile of A_TILE_BYTES
-// holding the high digits and then the low digits, each 128 rows x 64 K fp16
-// in the 128-byte swizzled K-major layout, byte for byte what the converter
-// warps write into a slot.  Entries outside the matrix become digits of 0.
-// With pre != 0 each entry is first reduced modulo mod.p (a residue pass).
+// tiles for one modulus p <= 65536: per (m-tile, k-block) the two 8-bit digit
+// planes described at A8_TILE_BYTES.  Entries outside the matrix are 0
+// (bytes 0x80, 0x80).  With pre != 0 each entry is first reduced modulo p (a
+// residue pass).  Thread q of a tile handles 4 consecutive K of one row.
 __global__ void __launch_bounds__(256)
     k_block_prep_a(const uint32_t *__restrict__ A, uint64_t lda, uint64_t m, uint64_t k, Mod mod,
-                   uint32_t half, uint32_t pre_magic, int pre, uint32_t kblocks, uint8_t *img)
+                   uint32_t pre_magic, int pre, uint32_t kblocks, uint8_t *img)
 {
     const uint64_t tile = blockIdx.x;   // mt * kblocks + kb
     const uint64_t mt = tile / kblocks, kb = tile % kblocks;
-    uint8_t *th = img + tile * A_TILE_BYTES;
-    uint8_t *tl = th + A_DIGIT_BYTES;
+    uint8_t *hi = img + tile * A8_TILE_BYTES;
+    uint8_t *lo = hi + A8_PLANE_BYTES;
+    const uint32_t p = mod.p;
+    const uint32_t thr = min((p - 1) / 2, 32639u);   // largest residue kept as itself
     for (int q = threadIdx.x; q < BM * 16; q += blockDim.x) {
         const int row = q >> 4, c4 = q & 15;
         const uint64_t gr = mt * BM + row, gk = kb * BK + (uint64_t)c4 * 4;
-        uint32_t v[4];
+        uint32_t hb = 0, lb = 0;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            v[e] = (gr < m && gk + e < k) ? __ldg(A + gr * lda + gk + e) : 0u;
-            if (pre) v[e] = reduce_small(v[e], mod.p, pre_magic);
+            uint32_t v = (gr < m && gk + e < k) ? __ldg(A + gr * lda + gk + e) : 0u;
+            if (pre) v = reduce_small(v, p, pre_magic);
+            const uint32_t u = v + 32896u - (v > thr ? p : 0u);   // in [0, 65535]
+            hb |= (u >> 8) << (8 * e);
+            lb |= (u & 255u) << (8 * e);
         }
-        uint32_t h01, l01, h23, l23;
-        split_pair(v[0], v[1], mod.p, half, h01, l01);
-        split_pair(v[2], v[3], mod.p, half, h23, l23);
-        const int j = c4 >> 1, halfsel = c4 & 1;
-        const uint32_t off = (uint32_t)row * 128u + ((uint32_t)(j ^ (row & 7)) << 4) + (halfsel << 3);
-        *reinterpret_cast<uint2 *>(th + off) = make_uint2(h01, h23);
-        *reinterpret_cast<uint2 *>(tl + off) = make_uint2(l01, l23);
+        *reinterpret_cast<uint32_t *>(hi + row * BK + c4 * 4) = hb;
+        *reinterpret_cast<uint32_t *>(lo + row * BK + c4 * 4) = lb;
     }
 }
 
@@ -664,7 +729,7 @@ __device__ __forceinline__ uint32_t mod_small64(uint64_t x, uint32_t m, uint64_t
 // C = X mod p, where X is the unique integer in [0, prod m_l) with X = R[l]
 // mod m_l: mixed-radix digits v_l in [0, m_l), X = v_0 + m_0 (v_1 + m_1 (v_2
 // + ...)), evaluated modulo p from the innermost term out.  The moduli are
-// the largest primes <= 65791, all above 65000, so a digit v_j < m_j is below
+// the largest primes <= 65536, all above 65000, so a digit v_j < m_j is below
 // 2 m_l and reduces modulo m_l by one conditional subtraction.
 __global__ void k_block_crt(const uint32_t *R, uint64_t m, uint64_t nb, uint32_t *C, uint64_t ldc, RnsConst rc)
 {
@@ -785,7 +850,8 @@ static uint32_t pow_mod_small(uint64_t b, uint64_t e, uint32_t m)
 
 bool block_rns_plan(uint32_t p, uint64_t k, RnsConst *rc)
 {
-    // the RNS_MAX largest primes not above BLOCK_TC_MAX_P, by trial division
+    // the RNS_MAX largest primes not above 65536, by trial division: every
+    // residue modulus then also fits the 8-bit digit planes of a prepared A
     static uint32_t primes[RNS_MAX];
     static bool ready = false;
     static std::mutex mu;
@@ -793,7 +859,7 @@ bool block_rns_plan(uint32_t p, uint64_t k, RnsConst *rc)
         std::lock_guard<std::mutex> g(mu);
         if (!ready) {
             int found = 0;
-            for (uint32_t c = BLOCK_TC_MAX_P; found < RNS_MAX; --c) {
+            for (uint32_t c = RNS_PRIME_MAX; found < RNS_MAX; --c) {
                 bool prime = c > 1;
                 for (uint32_t d = 2; prime && d * d <= c; ++d) prime = (c % d) != 0;
                 if (prime) primes[found++] = c;
@@ -866,7 +932,7 @@ size_t block_prep_a_bytes(uint64_t m, uint64_t k)
 {
     const uint64_t kblocks = (k + blk::BK - 1) / blk::BK;
     const uint64_t m_tiles = (m + blk::BM - 1) / blk::BM;
-    return (size_t)(m_tiles * kblocks) * blk::A_TILE_BYTES;
+    return (size_t)(m_tiles * kblocks) * blk::A8_TILE_BYTES;
 }
 
 cudaError_t launch_block_prep_a(const Mod &mod, uint64_t m, uint64_t k, const uint32_t *A,
@@ -876,9 +942,10 @@ cudaError_t launch_block_prep_a(const Mod &mod, uint64_t m, uint64_t k, const ui
     const uint64_t kblocks = (k + BK - 1) / BK, m_tiles = (m + BM - 1) / BM;
     if (m_tiles * kblocks == 0) return cudaSuccess;
     if (m_tiles * kblocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    if (mod.p > DIGIT8_MAX_P) return cudaErrorInvalidValue;
     k_block_prep_a<<<(unsigned)(m_tiles * kblocks), 256, 0, s>>>(
-        A, lda, m, k, mod, (mod.p - 1) / 2, (uint32_t)((1ull << 32) / mod.p), reduce_inputs ? 1 : 0,
-        (uint32_t)kblocks, img);
+        A, lda, m, k, mod, (uint32_t)((1ull << 32) / mod.p), reduce_inputs ? 1 : 0, (uint32_t)kblocks,
+        img);
     return cudaGetLastError();
 }
 

@@ -122,12 +122,15 @@ cudaError_t launch_matvec(Repr r, const Mod &m, uint64_t k, uint64_t rows, uint6
 // Block product (gfp_block.cu).  The tensor-core path needs the centred
 // residues to fit two balanced 8-bit digits: (p-1)/2 <= 32895.
 constexpr uint32_t BLOCK_TC_MAX_P = 65791;
+// Moduli of the residue passes, and of prepared operands taken directly: at
+// most 65536, so that every residue has two 8-bit balanced digits.
+constexpr uint32_t RNS_PRIME_MAX = 65536;
 bool block_tc_eligible(uint32_t p, const uint32_t *A, uint64_t lda);
 // A's layout suits the tensor-core kernel (TMA: 16-byte base, rows 16-byte apart)
 bool block_tc_layout_ok(const uint32_t *A, uint64_t lda);
 
 // Residue-number-system constants of a large-p tensor-core block product:
-// moduli mod[0..L-1] (primes <= BLOCK_TC_MAX_P), inv[l][j] = mod[j]^-1 mod
+// moduli mod[0..L-1] (primes <= RNS_PRIME_MAX), inv[l][j] = mod[j]^-1 mod
 // mod[l] for j < l, and the target modulus p.
 constexpr int RNS_MAX = 6;
 struct RnsConst {

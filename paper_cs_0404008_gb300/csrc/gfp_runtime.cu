@@ -874,7 +874,7 @@ GFP_API gfp_status gfp_matmul_block(gfp_ctx *ctx, uint32_t p, uint64_t m, uint64
 struct gfp_block_prep {
     uint32_t p = 0;
     uint64_t m = 0, k = 0;
-    int passes = 0;          // 1: p <= 65791 directly; more: residue passes
+    int passes = 0;          // 1: p <= 65536 directly; more: residue passes
     RnsConst rc{};
     void *mem = nullptr;
     size_t per = 0;          // bytes of one image
@@ -890,7 +890,7 @@ GFP_API gfp_status gfp_block_prepare(gfp_ctx *ctx, uint32_t p, uint64_t m, uint6
         return GFP_ERR_INVALID;
     RnsConst rc{};
     int passes = 1;
-    if (p > BLOCK_TC_MAX_P) {
+    if (p > RNS_PRIME_MAX) {   // beyond the 8-bit digit planes: residue passes
         if (!block_rns_plan(p, k, &rc)) return GFP_ERR_UNSUPPORTED;
         passes = rc.L;
     }

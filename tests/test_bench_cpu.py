@@ -21,12 +21,15 @@ def _primes_desc(limit, count):
 
 @pytest.mark.parametrize("p,k", [(65521, 16384), (65791, 16384), (65797, 16384), (2147483647, 16384),
                                  (4294967291, 16384), (4294967291, 1), (1000003, 100000)])
-def test_rns_passes_is_the_minimal_cover(p, k):
-    L = bench.rns_passes(p, k)
-    if p <= 65791:
+@pytest.mark.parametrize("direct_max", [65791, 65536])
+def test_rns_passes_is_the_minimal_cover(p, k, direct_max):
+    """Residue moduli are the largest primes <= 65536; the direct range is
+    p <= 65791 for uint32 A and p <= 65536 for a prepared A."""
+    L = bench.rns_passes(p, k, direct_max)
+    if p <= direct_max:
         assert L == 1
         return
-    primes = _primes_desc(65791, 8)
+    primes = _primes_desc(65536, 8)
     bound = k * (p - 1) ** 2
     prod = 1
     for q in primes[:L]:

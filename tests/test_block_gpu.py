@@ -366,7 +366,8 @@ def test_bounded_wait_expires_and_context_survives(lib, fresh):
 @pytest.mark.parametrize("shape", SHAPES_TC)
 @pytest.mark.parametrize("p", [2, 251, 65521, 65789, 2147483647, 4294967291])
 def test_block_prepared_parity(lib, fresh, p, shape):
-    """A prepared once (digit images, one per residue modulus for p > 65791),
+    """A prepared once (8-bit digit planes, one image per residue modulus for
+    p > 65536),
     then two products with different B: both equal the oracle and the
     unprepared product.  Ragged row tiles, ragged k-blocks and exact chunks,
     ragged column tiles; any row stride of A (the preparation reads A with
@@ -380,14 +381,16 @@ def test_block_prepared_parity(lib, fresh, p, shape):
     assert np.array_equal(got[1], oracle.block(p, A, B2)), (p, shape)
 
 
-@pytest.mark.parametrize("p", [65521, 65789, 4294967291])
+@pytest.mark.parametrize("p", [257, 65521, 65536, 65789, 4294967291])
 def test_block_prepared_extreme_digits(lib, fresh, p):
-    """Entries at the ends of the centred range ((p-1)/2 and (p+1)/2, the
-    largest digit magnitudes) and all (p-1), over 5000 terms (five exact
-    chunks)."""
+    """A's entries at both ends of its representatives (t = min((p-1)/2,
+    32639) kept as itself, t + 1 taken as t + 1 - p: digits 127 and -128),
+    B's at the ends of the centred range, and all (p-1), over 5000 terms
+    (five exact chunks)."""
     m, k, nb = 256, 5000, 64
     h = (p - 1) // 2
-    for a_val, b_val in ((h, h), (h + 1, h + 1), (h, h + 1), (p - 1, p - 1)):
+    t = min(h, 32639)
+    for a_val, b_val in ((t, h), (t + 1, h + 1), (t, h + 1), (t + 1, h), (p - 1, p - 1)):
         A = np.full((m, k), a_val, np.uint32)
         B = np.full((k, nb), b_val, np.uint32)
         want = oracle.block(p, A[:1], B)
@@ -400,7 +403,7 @@ def test_block_prepared_info_and_errors(lib, fresh):
     A = dev2(gi.uniform(65521, m * k, 63, 0).reshape(m, k))
     prep = lib.BlockPrep(fresh, 65521, A)
     kb, mt = (k + 63) // 64, (m + 127) // 128
-    assert prep.info() == (mt * kb * 32768, 1)
+    assert prep.info() == (mt * kb * 16384, 1)   # two 8-bit planes per 128 x 64 tile
     B = dev2(gi.uniform(65521, (k + 1) * 8, 63, 1).reshape(k + 1, 8))
     C = torch.zeros((m, 8), dtype=torch.int32, device="cuda")
     with pytest.raises(ValueError):
