@@ -881,6 +881,10 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                 "gpu_launches": 2 if passes == 1 else 2 * passes + 1,
             })
             ppasses = rns_passes(p, k, 65536)
+            ptf = ppasses * 4 * 2 * macs / (t_prep / 1e3) / 1e12
+            pk = peaks() or {}
+            tpk, tpk_kind = ((float(pk["bf16_tflops"]), "measured bf16_tflops (burst)")
+                             if pk.get("bf16_tflops") else (1900.0, "fallback bf16 dense"))
             pbytes = prep_bytes + ppasses * 4.0 * k * nb + 4.0 * m * nb
             if ppasses > 1:
                 pbytes += 2 * ppasses * 4.0 * m * nb
@@ -890,12 +894,16 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                 "what": "A prepared once into 8-bit digit planes (2 bytes per entry per pass), "
                         "then one product per call (B digits + tensor-core kernel widening "
                         "A's digits in shared memory)",
-                "roofline": with_read_peak({"bound": "hbm", "achieved": pach, "peak": peak,
-                                            "unit": "GB/s", "frac": pach / peak,
-                                            "kernel": "k_block_tc (prepared A) + k_block_prep_b",
-                                            "traffic": (traffic_for("k_block_tc_prepared", pbytes)
-                                                        if ppasses == 1 else None),
-                                            "peak_kind": f"{peak_kind} hbm_gbs"})}
+                "roofline": {"bound": "tensor", "achieved": ptf, "peak": tpk, "unit": "TFLOP/s",
+                             "frac": ptf / tpk, "kernel": "k_block_tc (prepared A) + k_block_prep_b",
+                             "peak_kind": tpk_kind,
+                             "what": "fp16 digit products (4 per multiply-add, 2 flops each) against "
+                                     "the measured bf16 dense rate (fp16 runs at the same rate)",
+                             "hbm": with_read_peak({"bound": "hbm", "achieved": pach, "peak": peak,
+                                                    "unit": "GB/s", "frac": pach / peak,
+                                                    "traffic": (traffic_for("k_block_tc_prepared", pbytes)
+                                                                if ppasses == 1 else None),
+                                                    "peak_kind": f"{peak_kind} hbm_gbs"})}}
             if large:
                 line["p_2^31-1"] = {n: {"ms": v, "gmacs": macs / (v / 1e3) / 1e9} for n, v in large.items()}
                 del Al, Bl
