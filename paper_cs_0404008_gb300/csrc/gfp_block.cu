@@ -76,15 +76,9 @@ constexpr uint32_t IDESC = ptx::idesc_f16_f32(BM, MMA_N);
 // two-k-block slots (longer TMA row bursts) and two B stages; prepared digits
 // only stream through, and four one-k-block slots with four B stages suit
 // them (16384 x 16384 x 64: 0.192 ms against 0.226 ms).
-// KSPLIT = 2: the two accumulator sets of TMEM serve one chunk together,
-// alternate K-steps going to alternate sets (four independent MMA chains
-// instead of two, each half as long); the epilogue adds the sets.  The sets
-// then no longer alternate between chunks, so the MMAs of the next chunk
-// wait for the drain: worth it only where the MMA chains are the bound.
-template <int SLOTS_, int BSTAGES_, int KBB_, int KSPLIT_ = 1>
+template <int SLOTS_, int BSTAGES_, int KBB_>
 struct Pipe {
-    static constexpr int SLOTS = SLOTS_, BSTAGES = BSTAGES_, KBB = KBB_, KSPLIT = KSPLIT_;
-    static_assert(KSPLIT == 1 || KSPLIT == 2, "one or two accumulator sets per chunk");
+    static constexpr int SLOTS = SLOTS_, BSTAGES = BSTAGES_, KBB = KBB_;
     static constexpr int SLOT_BYTES = KBB * A_TILE_BYTES;
     struct Bars {
         uint64_t a_full[SLOTS];    // A tile landed (1 arrival + tx bytes)
@@ -105,7 +99,7 @@ struct Pipe {
     static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 };
 using PipeU32 = Pipe<3, 2, 2>;    // uint32 A, converted in place
-using PipePrep = Pipe<4, 4, 1, 2>;   // prepared A: 8-bit digit planes, widened in place
+using PipePrep = Pipe<4, 4, 1>;   // prepared A: 8-bit digit planes, widened in place
 static_assert(PipePrep::KBB == 1, "one prepared tile per slot");
 
 // Prepared A (gfp_block_prepare): per (m-tile, k-block) two planes of 8-bit
@@ -315,7 +309,7 @@ __device__ __forceinline__ void widen_store(uint8_t *slot, int c, uint4 w)
 template <bool PRE, bool PREP, class P>
 __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__ Args a)
 {
-    constexpr int SLOTS = P::SLOTS, BSTAGES = P::BSTAGES, KBB = P::KBB, KSPLIT = P::KSPLIT;
+    constexpr int SLOTS = P::SLOTS, BSTAGES = P::BSTAGES, KBB = P::KBB;
     constexpr int SLOT_BYTES = P::SLOT_BYTES;
     using Bars = typename P::Bars;
     extern __shared__ uint8_t smem_raw[];
@@ -443,9 +437,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
             uint64_t idx = 0;
             for (uint64_t u = u0; u < u1 && ok; ++u, ++idx) {
                 const UnitPos q = unit_pos(a, u);
-                // accumulator set of this chunk (KSPLIT = 2: both, always set 0's barriers)
-                const uint32_t b = KSPLIT == 2 ? 0u : (uint32_t)(idx & 1);
-                const uint32_t use = KSPLIT == 2 ? (uint32_t)idx : (uint32_t)(idx >> 1);
+                const uint32_t b = (uint32_t)(idx & 1), use = (uint32_t)(idx >> 1);
                 if (use > 0 &&
                     !wait_bar(ptx::smem_u32(&bars->acc_empty[b]), (use - 1) & 1, abort, a.err)) {
                     ok = false;
@@ -472,12 +464,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                     const uint64_t db = ptx::sdesc_k_sw128(ptx::smem_u32(bst + (size_t)sb * B_TILE_BYTES));
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
-                        // KSPLIT = 2: K-step kk accumulates into set kk mod 2
-                        const uint32_t set = KSPLIT == 2 ? (uint32_t)(kk & 1) * 256u : 0u;
-                        const uint32_t acc = (kb > q.kb0 || kk >= KSPLIT) ? 1u : 0u;
+                        const uint32_t acc = (kb > q.kb0 || kk > 0) ? 1u : 0u;
                         // advance 16 fp16 (32 bytes) along K inside the swizzle atom
-                        ptx::mma_f16(d_hi + set, dah + 2 * kk, db + 2 * kk, IDESC, acc);
-                        ptx::mma_f16(d_lo + set, dal + 2 * kk, db + 2 * kk, IDESC, acc);
+                        ptx::mma_f16(d_hi, dah + 2 * kk, db + 2 * kk, IDESC, acc);
+                        ptx::mma_f16(d_lo, dal + 2 * kk, db + 2 * kk, IDESC, acc);
                     }
                     ptx::mma_commit(ptx::smem_u32(&bars->empty_b[sb]));
                     if (sub == KBB - 1 || kb + 1 == q.kb1) {   // last k-block of this slot
@@ -567,8 +557,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
         uint64_t idx = 0;
         for (uint64_t u = u0; u < u1; ++u, ++idx) {
             const UnitPos q = unit_pos(a, u);
-            const uint32_t b = KSPLIT == 2 ? 0u : (uint32_t)(idx & 1);
-            const uint32_t use = KSPLIT == 2 ? (uint32_t)idx : (uint32_t)(idx >> 1);
+            const uint32_t b = (uint32_t)(idx & 1), use = (uint32_t)(idx >> 1);
             const bool got = warp_wait(ptx::smem_u32(&bars->acc_full[b]), use & 1, abort, a.err);
             // decide together: the epilogue warps meet at named barriers below
             if (ptx::bar_red_or<1, EPI_WARPS * 32>(!got || *abort != 0)) break;
@@ -583,22 +572,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                 ptx::tmem_ld8(d_lo + g * 8, lh);
                 ptx::tmem_ld8(d_lo + NT + g * 8, ll);
                 ptx::tmem_ld_wait();
-                if (KSPLIT == 2) {
-                    // add the second set: integers below 2^23 in magnitude each,
-                    // so the fp32 sums (below 2^24) are exact
-                    uint32_t* const dst[4] = {hh, hl, lh, ll};
-                    const uint32_t src[4] = {d_hi + 256u + g * 8, d_hi + 256u + NT + g * 8,
-                                             d_lo + 256u + g * 8, d_lo + 256u + NT + g * 8};
-#pragma unroll
-                    for (int t4 = 0; t4 < 4; ++t4) {
-                        uint32_t t[8];
-                        ptx::tmem_ld8(src[t4], t);
-                        ptx::tmem_ld_wait();
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            dst[t4][j] = __float_as_uint(__uint_as_float(dst[t4][j]) + __uint_as_float(t[j]));
-                    }
-                }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const long long vhh = __float2int_rn(__uint_as_float(hh[j]));
