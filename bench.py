@@ -221,7 +221,8 @@ def traffic_record(kernel: str):
 def source_hash(files) -> str:
     """SHA-256 of the sources a traffic record was captured from, as the
     release build compiles them: blocks under `#ifdef GFP_DEVICE_CHECKS`,
-    `GFP_DCHECK(` lines and blank lines are left out."""
+    `GFP_DCHECK(` lines, whole-line `//` comments and blank lines are left
+    out."""
     h = hashlib.sha256()
     for f in files:
         skip = False
@@ -233,7 +234,7 @@ def source_hash(files) -> str:
             if skip:
                 skip = not st.startswith("#endif")
                 continue
-            if not st or "GFP_DCHECK(" in line:
+            if not st or st.startswith("//") or "GFP_DCHECK(" in line:
                 continue
             h.update(line.encode())
     return h.hexdigest()

@@ -14,12 +14,14 @@
 //   reduced mod p, and summed as residues.  Nothing is approximated.
 //   Roles per CTA (one CTA per SM, persistent over (tile, chunk) units):
 //     warp 0      TMA-loads uint32 A boxes (two 64-deep k-blocks per slot)
-//                 from HBM into a ring of shared-memory slots
+//                 from HBM into a ring of shared-memory slots (a prepared A:
+//                 bulk-copies its 8-bit digit planes, one k-block per slot)
 //     warp 1      owns TMEM and issues the MMAs (one thread)
 //     warp 2      bulk-copies the pre-split B digit tiles (own ring)
 //     warps 3-10  read a landed A box into registers, centre and split it,
 //                 and write the two fp16 digit tiles in place over it
 //                 (128-byte-swizzled, K-major), the same 32 KiB per k-block
+//                 (a prepared A: widen its 8-bit digits to the same tiles)
 //     warps 11-14 drain the accumulators (tcgen05.ld), recombine, reduce
 //   B's digits are stacked [hi | lo] along N (N = 128 per MMA), so one MMA
 //   per A digit yields both products with that digit; the two MMAs of a K
@@ -72,10 +74,10 @@ constexpr uint32_t IDESC = ptx::idesc_f16_f32(BM, MMA_N);
 // Pipeline depths: SLOTS shared-memory slots of KBB k-blocks of A each, and
 // BSTAGES B digit tiles.  A slot receives a uint32 box (TMA) that the
 // converter warps turn into fp16 digit tiles in place, or, for a prepared A,
-// ready digit tiles (bulk copy).  The uint32 path measured fastest with three
-// two-k-block slots (longer TMA row bursts) and two B stages; prepared digits
-// only stream through, and four one-k-block slots with four B stages suit
-// them (16384 x 16384 x 64: 0.192 ms against 0.226 ms).
+// a tile of 8-bit digit planes (bulk copy) that they widen in place.  The
+// uint32 path measured fastest with three two-k-block slots (longer TMA row
+// bursts) and two B stages; the prepared path with four one-k-block slots
+// and four B stages.
 template <int SLOTS_, int BSTAGES_, int KBB_>
 struct Pipe {
     static constexpr int SLOTS = SLOTS_, BSTAGES = BSTAGES_, KBB = KBB_;

@@ -48,8 +48,9 @@ def test_traffic_records_follow_their_sources(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.traffic_for("k_test", 1000.0) == pytest.approx(1250.0)
     assert bench.traffic_for("k_other", 1000.0) is None
-    # lines only a device-checks build compiles leave the record valid
-    src.write_text("kernel v1\n\n    GFP_DCHECK(w, c, 1u);\n#ifdef GFP_DEVICE_CHECKS\nx\n#endif\n")
+    # comment lines and lines only a device-checks build compiles leave the record valid
+    src.write_text("kernel v1\n\n    GFP_DCHECK(w, c, 1u);\n#ifdef GFP_DEVICE_CHECKS\nx\n#endif\n"
+                   "    // a comment\n")
     assert bench.traffic_for("k_test", 1000.0) == pytest.approx(1250.0)
     src.write_text("kernel v2\n")            # the kernel changed since the capture
     assert bench.traffic_for("k_test", 1000.0) is None
