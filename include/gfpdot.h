@@ -216,7 +216,7 @@ GFP_API gfp_status gfp_dot_batched_host(gfp_ctx *ctx, uint64_t count, const uint
  * Limits: count <= 1024 pairs and at most 16384 work units of 65536
  * elements (about 2^30 elements in total); beyond either, GFP_ERR_INVALID
  * with nothing enqueued.  The first call on a device looks up the array's
- * device address; make that first call before any stream capture.  All calls
+ * device address (a failure there is returned as GFP_ERR_CUDA).  All calls
  * share the array (each clears the parts that must start at zero): calls
  * whose work overlaps on the GPU race, so order them on one stream. */
 GFP_API gfp_status gfp_dot_batched_noalloc(const gfp_dot_desc *d, uint64_t count, uint32_t *out,
