@@ -874,12 +874,12 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
                                        f"uint32 uniform residues, {path}",
                            "l2": "A is larger than L2" if m * k * 4 > (129 << 20) else "A fits L2"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "kernel": "k_block_tc (+k_block_prep_b)",
+                             "frac": achieved / peak, "kernel": "k_block_tc (+k_block_prep_b, k_block_finish)",
                              "traffic": traffic_for("k_block_tc", abytes) if passes == 1 else None,
                              "peak_kind": f"{peak_kind} hbm_gbs",
                              "tensor_tflops_fp16": tflops},
                 "same_gpu": {n: {"ms": v, "gmacs": macs / (v / 1e3) / 1e9} for n, v in res.items()},
-                "gpu_launches": 2 if passes == 1 else 2 * passes + 1,
+                "gpu_launches": 3 if passes == 1 else 3 * passes + 1,
             })
             ppasses = rns_passes(p, k, 65536)
             ptf = ppasses * 4 * 2 * macs / (t_prep / 1e3) / 1e12
@@ -893,10 +893,10 @@ def measure_secondary(args, workload, g, torch, ctx, stream):
             line["prepared"] = {
                 "ms": t_prep, "gmacs": macs / (t_prep / 1e3) / 1e9, "passes": prep_passes,
                 "what": "A prepared once into 8-bit digit planes (2 bytes per entry per pass), "
-                        "then one product per call (B digits + tensor-core kernel widening "
-                        "A's digits in shared memory)",
+                        "then one product per call (B digits, tensor-core kernel widening "
+                        "A's digits in shared memory, partial sums to C)",
                 "roofline": {"bound": "tensor", "achieved": ptf, "peak": tpk, "unit": "TFLOP/s",
-                             "frac": ptf / tpk, "kernel": "k_block_tc (prepared A) + k_block_prep_b",
+                             "frac": ptf / tpk, "kernel": "k_block_tc (prepared A) + k_block_prep_b + k_block_finish",
                              "peak_kind": tpk_kind,
                              "what": "fp16 digit products (4 per multiply-add, 2 flops each) against "
                                      "the measured bf16 dense rate (fp16 runs at the same rate)",

@@ -26,9 +26,11 @@
 //   B's digits are stacked [hi | lo] along N (N = 128 per MMA), so one MMA
 //   per A digit yields both products with that digit; the two MMAs of a K
 //   step accumulate into separate TMEM columns (two independent chains).
-//   Units of one output tile may be split over two CTAs; their residue sums
-//   meet in a u32 workspace through atomics and the CTA that completes a
-//   tile (ticket counter) reduces it into C and clears the workspace.
+//   Units of one output tile may be split over several CTAs: each adds its
+//   residue sums for the tile into a column-major u32 workspace (coalesced
+//   atomics, one transaction per column and warp), and a small kernel behind
+//   this one reduces the sums mod p, writes C through a shared-memory
+//   transpose and clears the workspace.
 //
 // Larger moduli on the tensor cores (p > 65791): the exact integer products
 // sum_t A[i][t] B[t][j] are below k (p-1)^2, so they are fixed by their
@@ -93,7 +95,6 @@ struct Pipe {
         uint64_t drain;            // all MMAs issued by this CTA completed
         uint32_t tmem_base;
         uint32_t abort;
-        uint32_t last_flag;
     };
     static constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + (size_t)SLOTS * SLOT_BYTES +
                                          (size_t)BSTAGES * B_TILE_BYTES + 1024;
@@ -122,8 +123,8 @@ struct Args {
     const uint8_t *Aimg;      // prepared A: [m_tiles][kblocks] tiles of A8_TILE_BYTES (PREP)
     uint32_t *C;
     uint64_t ldc;
-    uint32_t *Cacc;           // m x (n_tiles*NT) u32 partial residue sums (zero outside calls)
-    uint32_t *tickets;        // n_tiles*m_tiles chunk counters (zero outside calls)
+    uint32_t *Cacc;           // (n_tiles*NT) x m u32 partial residue sums, column-major: the
+                              // entry of row i, column j at j*m + i (zero outside calls)
     uint32_t *err;            // bit 0: a bounded wait expired
     Mod mod;
     uint64_t off;             // multiple of p >= 2^41 making recombined values non-negative
@@ -304,6 +305,15 @@ __device__ __forceinline__ void widen_store(uint8_t *slot, int c, uint4 w)
     *reinterpret_cast<uint4 *>(tile + base + (((uint32_t)(2 * j + 1) ^ r7) << 4)) = make_uint4(o[4], o[5], o[6], o[7]);
 }
 
+// (x + y) mod p for x, y < p: the per-thread sums of chunk residues stay
+// below p however many chunks a long K holds, and the u32 partial sums that
+// meet in the workspace then add at most one such sum per contributing CTA
+__device__ __forceinline__ uint32_t add_mod(uint32_t x, uint32_t y, uint32_t p)
+{
+    const uint32_t t = x + y;
+    return t >= p ? t - p : t;
+}
+
 // PRE: reduce each input modulo p while splitting it (the residue passes).
 // PREP: A arrives prepared, as 8-bit digit planes (k_block_prep_a); the
 // producer bulk-copies a 16 KiB tile into the upper half of a slot and the
@@ -340,7 +350,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
         }
         ptx::mbar_init(ptx::smem_u32(&bars->drain), 1);
         bars->abort = 0;
-        bars->last_flag = 0;
         ptx::fence_barrier_init();
     }
     if (warp == W_MMA) {
@@ -555,7 +564,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
         uint32_t res[NT];
 #pragma unroll
         for (int j = 0; j < NT; ++j) res[j] = 0;
-        uint32_t seg_chunks = 0;
         uint64_t idx = 0;
         for (uint64_t u = u0; u < u1; ++u, ++idx) {
             const UnitPos q = unit_pos(a, u);
@@ -581,13 +589,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                                          (long long)__float2int_rn(__uint_as_float(lh[j]));
                     const long long vll = __float2int_rn(__uint_as_float(ll[j]));
                     const long long v = vhh * 65536ll + vx * 256ll + vll;
-                    res[g * 8 + j] += reduce64((uint64_t)(v + (long long)a.off), a.mod);
+                    res[g * 8 + j] = add_mod(res[g * 8 + j], reduce64((uint64_t)(v + (long long)a.off), a.mod),
+                                             a.mod.p);
                 }
             }
             ptx::tc_fence_before();
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&bars->acc_empty[b]));
-            ++seg_chunks;
             // end of this CTA's run of units on the output tile?
             bool flush = (u + 1 == u1);
             if (!flush) {
@@ -595,55 +603,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                 flush = (nq.mt != q.mt) || (nq.nt != q.nt);
             }
             if (flush) {
+                // column-major partial sums: the 32 lanes of a warp (consecutive
+                // rows) add to 128 consecutive bytes, one L2 transaction per
+                // column; k_block_finish reduces them into C after this kernel
                 const uint64_t grow = (uint64_t)q.mt * BM + row_in_tile;
-                const uint64_t ldacc = (uint64_t)a.n_tiles * NT;
                 const uint64_t col0 = (uint64_t)q.nt * NT;
                 if (grow < a.m) {
 #pragma unroll
                     for (int j = 0; j < NT; ++j)
-                        if (col0 + j < a.nb) atomicAdd(&a.Cacc[grow * ldacc + col0 + j], res[j]);
+                        if (col0 + j < a.nb) atomicAdd(&a.Cacc[(col0 + j) * a.m + grow], res[j]);
                 }
 #pragma unroll
                 for (int j = 0; j < NT; ++j) res[j] = 0;
-                __threadfence();
-                asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32));
-                if (warp == W_EPI0 && lane == 0) {
-                    const uint32_t old = atomicAdd(&a.tickets[q.nt * a.m_tiles + q.mt], seg_chunks);
-                    bars->last_flag = (old + seg_chunks == a.chunks) ? 1u : 0u;
-                    __threadfence();
-                }
-                asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32));
-                if (bars->last_flag) {
-                    // every contribution to this tile is in L2 (atomics, then fences, then
-                    // the ticket): read the row with L2 loads issued together, reduce,
-                    // write C and clear the partial sums for the next call
-                    if (grow < a.m) {
-                        uint32_t *row = &a.Cacc[grow * ldacc + col0];   // 16-byte aligned
-                        uint4 v[NT / 4];
-#pragma unroll
-                        for (int q4 = 0; q4 < NT / 4; ++q4) v[q4] = __ldcg(reinterpret_cast<const uint4 *>(row) + q4);
-#pragma unroll
-                        for (int q4 = 0; q4 < NT / 4; ++q4)
-                            __stcg(reinterpret_cast<uint4 *>(row) + q4, make_uint4(0u, 0u, 0u, 0u));
-                        uint32_t *crow = a.C + grow * a.ldc + col0;
-#pragma unroll
-                        for (int q4 = 0; q4 < NT / 4; ++q4) {
-                            const uint32_t w[4] = {v[q4].x, v[q4].y, v[q4].z, v[q4].w};
-#pragma unroll
-                            for (int e = 0; e < 4; ++e)
-                                if (col0 + 4 * q4 + e < a.nb) crow[4 * q4 + e] = reduce64(w[e], a.mod);
-                        }
-                    }
-                    asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32));
-                    if (warp == W_EPI0 && lane == 0) {
-                        atomicExch(&a.tickets[q.nt * a.m_tiles + q.mt], 0u);
-                        bars->last_flag = 0;
-                    }
-                }
-                asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32));
-                seg_chunks = 0;
             }
         }
+        // the kernel that reduces the partial sums may be launched now (it
+        // waits for this grid to complete before reading them)
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     }
 
     ptx::tc_fence_before();
@@ -653,6 +629,38 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
         ptx::tmem_dealloc(tmem, TMEM_COLS);
     }
 }
+
+constexpr int FIN_THREADS = 256;
+__global__ void __launch_bounds__(FIN_THREADS)
+    k_block_finish(uint32_t *__restrict__ Cacc, uint64_t m, uint64_t nb, uint32_t *__restrict__ C,
+                   uint64_t ldc, Mod mod)
+{
+    __shared__ uint32_t t[NT][BM + 1];   // [column][row], padded against bank conflicts
+    constexpr int PER = NT * BM / FIN_THREADS;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const uint64_t r0 = (uint64_t)blockIdx.x * BM, c0 = (uint64_t)blockIdx.y * NT;
+    // all of a thread's loads are issued before any is used or cleared (one
+    // memory latency, not one per element); consecutive threads take
+    // consecutive rows of one column
+    uint32_t v[PER];
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+        const int i = threadIdx.x + e * FIN_THREADS, c = i / BM, r = i % BM;
+        v[e] = (r0 + r < m && c0 + c < nb) ? __ldcg(&Cacc[(c0 + c) * m + r0 + r]) : 0u;
+    }
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+        const int i = threadIdx.x + e * FIN_THREADS, c = i / BM, r = i % BM;
+        if (r0 + r < m && c0 + c < nb) __stcg(&Cacc[(c0 + c) * m + r0 + r], 0u);
+        t[c][r] = reduce64(v[e], mod);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NT * BM; i += FIN_THREADS) {
+        const int r = i / NT, c = i % NT;   // consecutive threads: consecutive columns of one row
+        if (r0 + r < m && c0 + c < nb) C[(r0 + r) * ldc + c0 + c] = t[c][r];
+    }
+}
+
 
 // B (k x nb, row-major) -> per (n-tile, k-block) tiles of 128 rows x 64 K
 // fp16 digits in the 128-byte swizzled K-major layout: rows 0..63 hold the
@@ -900,11 +908,9 @@ size_t block_tc_workspace_bytes(uint64_t m, uint64_t k, uint64_t nb)
 {
     const uint64_t kblocks = (k + blk::BK - 1) / blk::BK;
     const uint64_t n_tiles = (nb + blk::NT - 1) / blk::NT;
-    const uint64_t m_tiles = (m + blk::BM - 1) / blk::BM;
     size_t b = n_tiles * kblocks * (uint64_t)blk::B_TILE_BYTES;
     b = (b + 255) & ~(size_t)255;
     b += ((m * n_tiles * blk::NT * 4 + 255) & ~(size_t)255);
-    b += ((n_tiles * m_tiles * 4 + 255) & ~(size_t)255);
     b += 256;   // error flag
     return b;
 }
@@ -1002,6 +1008,7 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
     a.m_tiles = (uint32_t)((m + BM - 1) / BM);
     a.chunks = (a.kblocks + KC - 1) / KC;
     a.units = (uint64_t)a.n_tiles * a.m_tiles * a.chunks;
+    if (a.n_tiles > 65535) return cudaErrorInvalidValue;   // grid y of the finishing kernel
     const uint64_t two41 = 1ull << 41;
     a.off = (two41 / mod.p + 1) * (uint64_t)mod.p;
     a.pre_magic = (uint32_t)((1ull << 32) / mod.p);
@@ -1011,8 +1018,6 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
     a.Bimg = w;
     a.Cacc = (uint32_t *)(w + o);
     o += ((m * a.n_tiles * NT * 4 + 255) & ~(size_t)255);
-    a.tickets = (uint32_t *)(w + o);
-    o += ((a.n_tiles * a.m_tiles * 4 + 255) & ~(size_t)255);
     a.err = (uint32_t *)(w + o);
     k_block_prep_b<<<a.n_tiles * a.kblocks, 256, 0, s>>>(B, ldb, k, nb, mod, a.half, a.kblocks,
                                                          reduce_inputs ? 1 : 0, (uint8_t *)a.Bimg);
@@ -1039,7 +1044,15 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
         e = cudaLaunchKernelEx(&cfg, k_block_tc<false, false, PipeU32>, a);
     }
     if (e != cudaSuccess) return e;
-    *launches += 2;
+    cudaLaunchConfig_t fcfg = {};
+    fcfg.gridDim = dim3(a.m_tiles, a.n_tiles);
+    fcfg.blockDim = dim3(FIN_THREADS);
+    fcfg.stream = s;
+    fcfg.attrs = pdl;
+    fcfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&fcfg, k_block_finish, a.Cacc, m, nb, C, ldc, mod);
+    if (e != cudaSuccess) return e;
+    *launches += 3;
     return cudaGetLastError();
 }
 
