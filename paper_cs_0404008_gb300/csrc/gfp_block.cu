@@ -78,7 +78,7 @@ constexpr uint32_t IDESC = ptx::idesc_f16_f32(BM, MMA_N);
 // converter warps turn into fp16 digit tiles in place, or, for a prepared A,
 // a tile of 8-bit digit planes (bulk copy) that they widen in place.  The
 // uint32 path measured fastest with three two-k-block slots (longer TMA row
-// bursts) and two B stages; the prepared path with four one-k-block slots
+// bursts) and two B stages; the prepared path with five one-k-block slots
 // and four B stages.
 template <int SLOTS_, int BSTAGES_, int KBB_>
 struct Pipe {
@@ -102,7 +102,7 @@ struct Pipe {
     static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 };
 using PipeU32 = Pipe<3, 2, 2>;    // uint32 A, converted in place
-using PipePrep = Pipe<4, 4, 1>;   // prepared A: 8-bit digit planes, widened in place
+using PipePrep = Pipe<5, 4, 1>;   // prepared A: 8-bit digit planes, widened in place
 static_assert(PipePrep::KBB == 1, "one prepared tile per slot");
 
 // Prepared A (gfp_block_prepare): per (m-tile, k-block) two planes of 8-bit
