@@ -615,6 +615,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
                 }
 #pragma unroll
                 for (int j = 0; j < NT; ++j) res[j] = 0;
+                // the epilogue warps meet after a flush: without this barrier the
+                // compiler carries the flush into the next unit's drain and the
+                // kernel spills about 440 bytes per thread at 128 registers
+                asm volatile("bar.sync 1, %0;" ::"n"(EPI_WARPS * 32));
             }
         }
         // the kernel that reduces the partial sums may be launched now (it
