@@ -211,6 +211,30 @@ def test_block_many_units_per_cta(lib, fresh):
         assert np.array_equal(run_block(lib, fresh, p, A, B), oracle.block(p, A, B))
 
 
+def test_block_long_k_residue_sums_stay_below_2_32(lib):
+    """One output over K = 2^26 + 2^16 terms: 65600 exact 1024-term chunks,
+    each built to leave the residue p - 1 (A all ones, B the constant c with
+    1024 c = p - 1 mod p), so that the chunk residues of the output sum to
+    65600 (p - 1) > 2^32.  The tensor-core kernel keeps every running sum of
+    residues below p; a plain 32-bit sum of them would wrap.  Needs a 16 GiB
+    B digit image (one 16 KiB tile per 64-deep k-block), held by a context of
+    its own and freed with it."""
+    p = 65521
+    k = (1 << 26) + (1 << 16)
+    c = (p - 1) * pow(1024, -1, p) % p
+    A = np.ones((1, k), dtype=np.uint32)
+    B = np.full((k, 1), c, dtype=np.uint32)
+    want = oracle.block(p, A, B)
+    assert int(want[0, 0]) == (k // 1024) * (p - 1) % p   # the chunks as built
+    ctx = lib.Context(0)
+    try:
+        ctx.set_repr(lib.GFP_REPR_F16TC)
+        got = run_block(lib, ctx, p, A, B)
+        assert np.array_equal(got, want), (got, want)
+    finally:
+        ctx.close()
+
+
 def test_block_full_size_workload(lib, fresh):
     """The block workload: A 16384 x 16384, B 16384 x 64 over GF(65521),
     tensor-core path, every entry against the oracle."""
