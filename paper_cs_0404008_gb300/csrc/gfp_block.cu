@@ -634,10 +634,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_tc(const __grid_constant__
     }
 }
 
-constexpr int FIN_THREADS = 256;
+constexpr int FIN_THREADS = 512;
 __global__ void __launch_bounds__(FIN_THREADS)
     k_block_finish(uint32_t *__restrict__ Cacc, uint64_t m, uint64_t nb, uint32_t *__restrict__ C,
-                   uint64_t ldc, Mod mod)
+                   uint64_t ldc, uint32_t p, uint32_t magic)
 {
     __shared__ uint32_t t[NT][BM + 1];   // [column][row], padded against bank conflicts
     constexpr int PER = NT * BM / FIN_THREADS;
@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(FIN_THREADS)
     for (int e = 0; e < PER; ++e) {
         const int i = threadIdx.x + e * FIN_THREADS, c = i / BM, r = i % BM;
         if (r0 + r < m && c0 + c < nb) __stcg(&Cacc[(c0 + c) * m + r0 + r], 0u);
-        t[c][r] = reduce64(v[e], mod);
+        t[c][r] = reduce_small(v[e], p, magic);   // the sums are below 2^32
     }
     __syncthreads();
     for (int i = threadIdx.x; i < NT * BM; i += FIN_THREADS) {
@@ -1054,7 +1054,7 @@ cudaError_t launch_block_tc(const Mod &mod, uint64_t m, uint64_t k, uint64_t nb,
     fcfg.stream = s;
     fcfg.attrs = pdl;
     fcfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&fcfg, k_block_finish, a.Cacc, m, nb, C, ldc, mod);
+    e = cudaLaunchKernelEx(&fcfg, k_block_finish, a.Cacc, m, nb, C, ldc, mod.p, a.pre_magic);
     if (e != cudaSuccess) return e;
     *launches += 3;
     return cudaGetLastError();
