@@ -260,7 +260,8 @@ GFP_API gfp_status gfp_matvec_sequence(gfp_ctx *ctx, uint32_t p, uint64_t n, con
  * lda >= k, ldb >= nb, ldc >= nb; C must not overlap A or B.
  * Path: with GFP_REPR_AUTO or GFP_REPR_F16TC, A 16-byte aligned and lda a
  * multiple of 4, the tensor cores: for p <= 65791 the digit kernel directly
- * (two launches: B digit split, then the persistent product); for larger p
+ * (three launches: B digit split, the persistent product, the reduction of
+ * its partial sums into C); for larger p
  * one such pass per modulus of a residue number system (the L <= 6 largest
  * primes <= 65536 whose product exceeds k (p-1)^2, each pass reducing the
  * inputs modulo its prime) and one launch recombining the residues with
@@ -295,8 +296,8 @@ GFP_API gfp_status gfp_block_prepare(gfp_ctx *ctx, uint32_t p, uint64_t m, uint6
                                      const uint32_t *A, uint64_t lda, gfp_block_prep **out);
 /* C = A B mod p for the prepared A (m x k): B device k x nb (ldb >= nb),
  * C device m x nb (ldc >= nb); the same result as gfp_matmul_block on the
- * original A.  Two launches (B's digits, the product), or two per residue
- * pass plus one recombination.  Uses the context's block workspace (grown on
+ * original A.  Three launches (B's digits, the product, its partial sums
+ * into C), or three per residue pass plus one recombination.  Uses the context's block workspace (grown on
  * first use of a shape: make that call outside stream capture); calls sharing
  * one context must not run concurrently on different streams. */
 GFP_API gfp_status gfp_matmul_block_prepared(gfp_ctx *ctx, const gfp_block_prep *prep, uint64_t nb,

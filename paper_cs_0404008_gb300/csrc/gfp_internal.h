@@ -211,8 +211,8 @@ struct gfp_ctx {
     uint32_t *stage_out = nullptr;
     size_t stage_out_elems = 0;
 
-    // block-product workspace (B digit image, partial sums, tickets, error
-    // flag); zero outside calls except the B image; grown on demand
+    // block-product workspace (B digit image, column-major partial sums,
+    // error flag); zero outside calls except the B image; grown on demand
     void *blk_ws = nullptr;
     size_t blk_ws_bytes = 0;
     uint64_t blk_m = 0, blk_k = 0, blk_nb = 0;   // shape whose error flag is live
