@@ -297,9 +297,10 @@ GFP_API gfp_status gfp_block_prepare(gfp_ctx *ctx, uint32_t p, uint64_t m, uint6
 /* C = A B mod p for the prepared A (m x k): B device k x nb (ldb >= nb),
  * C device m x nb (ldc >= nb); the same result as gfp_matmul_block on the
  * original A.  Three launches (B's digits, the product, its partial sums
- * into C), or three per residue pass plus one recombination.  Uses the context's block workspace (grown on
- * first use of a shape: make that call outside stream capture); calls sharing
- * one context must not run concurrently on different streams. */
+ * into C), or three per residue pass plus one recombination.  Uses the
+ * context's block workspace (grown on first use of a shape: make that call
+ * outside stream capture); calls sharing one context must not run
+ * concurrently on different streams. */
 GFP_API gfp_status gfp_matmul_block_prepared(gfp_ctx *ctx, const gfp_block_prep *prep, uint64_t nb,
                                              const uint32_t *B, uint64_t ldb, uint32_t *C,
                                              uint64_t ldc, void *stream);
